@@ -1,0 +1,387 @@
+/*
+ * ppabc_oracle.c -- plain FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+ *
+ * The slow, obviously correct reference for the prior-predictive Monte Carlo
+ * path of Warne, Sisson & Drovandi (arXiv:1902.09046).  Every function follows
+ * one passage of the paper (cited at the function) or one published
+ * definition, in the paper's order, with no blocking, fusion or reordering.
+ * Loaded only by tests, the smoke check and the benchmark's CPU-baseline leg;
+ * it shares no code with the CUDA path.
+ *
+ * Threads (where a function takes n_threads) split the sample range into
+ * equal contiguous pieces, which is the static schedule the paper uses for its
+ * OpenMP prior-predictive sampler (Sec. 3.4).  Each sample depends only on its
+ * own counter, so the split changes no result.
+ */
+#include "ppabc_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon et al., SC'11, "Parallel random numbers: as easy as
+ * 1, 2, 3").  The paper needs independent streams per worker (Sec. 2.5); of
+ * its three options this is (ii), a generator that splits into sub-streams,
+ * here by the counter.  One round maps (c0,c1,c2,c3) with key (k0,k1) to
+ *   (hi(M1*c2) ^ c1 ^ k0,  lo(M1*c2),  hi(M0*c0) ^ c3 ^ k1,  lo(M0*c0))
+ * and the key is bumped by the Weyl constants between rounds.
+ * ------------------------------------------------------------------------- */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                       uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += PHILOX_W0;
+      k1 += PHILOX_W1;
+    }
+    uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    uint32_t n1 = (uint32_t)p1;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    uint32_t n3 = (uint32_t)p0;
+    c0 = n0;
+    c1 = n1;
+    c2 = n2;
+    c3 = n3;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+static void seed_to_key(uint64_t seed, uint32_t key[2]) {
+  key[0] = (uint32_t)(seed & 0xffffffffu);
+  key[1] = (uint32_t)(seed >> 32);
+}
+
+void orc_philox_batch(uint64_t seed, const uint32_t *ctr, uint64_t n,
+                      uint32_t *out) {
+  uint32_t key[2];
+  seed_to_key(seed, key);
+  for (uint64_t i = 0; i < n; ++i) orc_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
+/* u(w) = ((w >> 9) + 1/2) 2^-23: the midpoint of one of 2^23 equal cells of
+ * (0,1), never 0 or 1. */
+double orc_u01(uint32_t w) { return ((double)(w >> 9) + 0.5) * 0x1p-23; }
+
+/* Box-Muller transform (the paper draws its normals with MKL's Box-Muller
+ * method, Sec. 3.4): two uniforms give two independent standard normals. */
+static void box_muller(uint32_t w_even, uint32_t w_odd, double *z_even,
+                       double *z_odd) {
+  const double two_pi = 6.283185307179586476925286766559;
+  double u1 = orc_u01(w_even);
+  double u2 = orc_u01(w_odd);
+  double r = sqrt(-2.0 * log(u1));
+  *z_even = r * cos(two_pi * u2);
+  *z_odd = r * sin(two_pi * u2);
+}
+
+/* The four normals of counter block (b, c1, c2, tag). */
+static void block_normals(const uint32_t key[2], uint32_t b, uint32_t c1,
+                          uint32_t c2, uint32_t tag, double z[4]) {
+  uint32_t ctr[4] = {b, c1, c2, tag};
+  uint32_t w[4];
+  orc_philox4x32_10(ctr, key, w);
+  box_muller(w[0], w[1], &z[0], &z[1]);
+  box_muller(w[2], w[3], &z[2], &z[3]);
+}
+
+void orc_stream_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag,
+                        uint64_t j0, uint64_t n, double *z) {
+  uint32_t key[2];
+  seed_to_key(seed, key);
+  for (uint64_t t = 0; t < n; ++t) {
+    uint64_t j = j0 + t;
+    double zb[4];
+    block_normals(key, (uint32_t)(j / 4), c1, c2, tag, zb);
+    z[t] = zb[j % 4];
+  }
+}
+
+/* ---------------------------------------------------------------------------
+ * Prior-predictive sampling for ABC (Sec. 3.1, Eq. 2 and Algorithm 1, in the
+ * fixed-N form the paper describes after Algorithm 1), with the model
+ * simulated by the Euler-Maruyama scheme (Sec. 3.3, Eq. 5) applied to the
+ * Ornstein-Uhlenbeck SDE dX = th1 (th2 - X) dt + th3 dW.
+ *
+ * For sample i:
+ *   1. theta* ~ pi(theta): th_j = lo_j + (hi_j - lo_j) u(w_j), w = Philox
+ *      block (0, i, sub, PRIOR) (uniform priors, as in the paper's sampler).
+ *   2. D* ~ s(D; theta*): X_0 = x0 and for s = 1..S
+ *        X_s = X_{s-1} + th1 (th2 - X_{s-1}) dt + th3 sqrt(dt) xi_{s-1},
+ *      xi_j = normal j of stream (seed, i, sub, PATH).
+ *   3. S(D*): X at the observation steps s_j = floor(j S / n_obs),
+ *      j = 1..n_obs.
+ *   4. rho = Euclidean distance between S(D*) and the observed summaries.
+ * ------------------------------------------------------------------------- */
+static void ou_one_sample(const orc_ou_model *m, const double *y_obs,
+                          const uint32_t key[2], uint64_t i, uint32_t sub,
+                          double *theta, double *summ, double *dist) {
+  uint32_t prior_ctr[4] = {0u, (uint32_t)i, sub, ORC_TAG_PRIOR};
+  uint32_t w[4];
+  orc_philox4x32_10(prior_ctr, key, w);
+  double th[3];
+  for (int j = 0; j < 3; ++j) th[j] = m->lo[j] + (m->hi[j] - m->lo[j]) * orc_u01(w[j]);
+  if (theta) {
+    theta[0] = th[0];
+    theta[1] = th[1];
+    theta[2] = th[2];
+  }
+
+  const double dt = m->dt;
+  const double sqrt_dt = sqrt(dt);
+  const uint32_t S = m->n_steps, n_obs = m->n_obs;
+  double X = m->x0;
+  double acc = 0.0;
+  uint32_t j = 1;
+  uint64_t s_next = ((uint64_t)j * S) / n_obs;
+  double z[4];
+  for (uint32_t s = 1; s <= S; ++s) {
+    uint32_t jz = s - 1; /* index of the normal this step consumes */
+    if (jz % 4 == 0) block_normals(key, jz / 4, (uint32_t)i, sub, ORC_TAG_PATH, z);
+    double xi = z[jz % 4];
+    X = X + th[0] * (th[1] - X) * dt + th[2] * sqrt_dt * xi;
+    if (s == s_next) {
+      double r = X - y_obs[j - 1];
+      if (summ) summ[j - 1] = X;
+      acc += r * r;
+      ++j;
+      s_next = (j <= n_obs) ? ((uint64_t)j * S) / n_obs : 0;
+    }
+  }
+  *dist = sqrt(acc);
+}
+
+typedef struct ou_job {
+  const orc_ou_model *m;
+  const double *y_obs;
+  uint32_t key[2];
+  uint64_t base, lo, hi;
+  uint32_t sub;
+  double *theta, *summ, *dist;
+} ou_job;
+
+static void *ou_worker(void *arg) {
+  ou_job *J = (ou_job *)arg;
+  for (uint64_t t = J->lo; t < J->hi; ++t) {
+    ou_one_sample(J->m, J->y_obs, J->key, J->base + t, J->sub,
+                  J->theta ? J->theta + 3 * t : NULL,
+                  J->summ ? J->summ + (uint64_t)J->m->n_obs * t : NULL,
+                  J->dist + t);
+  }
+  return NULL;
+}
+
+int orc_ou_prior_predictive(const orc_ou_model *m, const double *y_obs,
+                            uint64_t base, uint64_t n, uint64_t seed,
+                            uint32_t sub, double *theta, double *summ,
+                            double *dist, int n_threads) {
+  if (!m || !y_obs || !dist) return -1;
+  if (m->n_obs == 0 || m->n_steps < m->n_obs || !(m->dt > 0.0)) return -1;
+  if (base + n > 0x100000000ull) return -1;
+  if (n_threads < 1) n_threads = 1;
+  if ((uint64_t)n_threads > n) n_threads = (int)(n > 0 ? n : 1);
+  ou_job *jobs = (ou_job *)calloc((size_t)n_threads, sizeof(ou_job));
+  pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+  if (!jobs || !th) {
+    free(jobs);
+    free(th);
+    return -1;
+  }
+  for (int t = 0; t < n_threads; ++t) {
+    ou_job *J = &jobs[t];
+    J->m = m;
+    J->y_obs = y_obs;
+    seed_to_key(seed, J->key);
+    J->base = base;
+    J->lo = n * (uint64_t)t / (uint64_t)n_threads;
+    J->hi = n * (uint64_t)(t + 1) / (uint64_t)n_threads;
+    J->sub = sub;
+    J->theta = theta;
+    J->summ = summ;
+    J->dist = dist;
+  }
+  for (int t = 1; t < n_threads; ++t) pthread_create(&th[t], NULL, ou_worker, &jobs[t]);
+  ou_worker(&jobs[0]);
+  for (int t = 1; t < n_threads; ++t) pthread_join(th[t], NULL);
+  free(jobs);
+  free(th);
+  return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Selection.  The paper fixes N and then picks epsilon a posteriori from the
+ * empirical distribution of the discrepancy (Sec. 3.1, after Algorithm 1):
+ * accepting the k nearest is choosing epsilon as the k-th smallest distance.
+ * Ties in distance are broken by the smaller sample index, so the accepted
+ * set always has exactly k members.  NaN distances sort after everything.
+ * ------------------------------------------------------------------------- */
+typedef struct dist_idx {
+  double d;
+  uint64_t i;
+} dist_idx;
+
+static int cmp_dist_idx(const void *a, const void *b) {
+  const dist_idx *x = (const dist_idx *)a, *y = (const dist_idx *)b;
+  int xn = isnan(x->d), yn = isnan(y->d);
+  if (xn != yn) return xn - yn;
+  if (!xn) {
+    if (x->d < y->d) return -1;
+    if (x->d > y->d) return 1;
+  }
+  return (x->i > y->i) - (x->i < y->i);
+}
+
+static int cmp_u64(const void *a, const void *b) {
+  uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+  return (x > y) - (x < y);
+}
+
+int orc_select_topk(const double *dist, uint64_t n, uint64_t k,
+                    uint64_t *idx_out) {
+  if (k > n) return -1;
+  if (k == 0) return 0;
+  dist_idx *a = (dist_idx *)malloc((size_t)n * sizeof(dist_idx));
+  if (!a) return -1;
+  for (uint64_t i = 0; i < n; ++i) {
+    a[i].d = dist[i];
+    a[i].i = i;
+  }
+  qsort(a, (size_t)n, sizeof(dist_idx), cmp_dist_idx);
+  for (uint64_t j = 0; j < k; ++j) idx_out[j] = a[j].i;
+  free(a);
+  qsort(idx_out, (size_t)k, sizeof(uint64_t), cmp_u64);
+  return 0;
+}
+
+/* Algorithm 1's acceptance test rho <= epsilon, applied to every sample. */
+uint64_t orc_select_eps(const double *dist, uint64_t n, double eps,
+                        uint64_t *idx_out) {
+  uint64_t c = 0;
+  for (uint64_t i = 0; i < n; ++i)
+    if (dist[i] <= eps) idx_out[c++] = i;
+  return c;
+}
+
+/* Posterior summaries of the accepted sample: mean, then the unbiased
+ * variance about that mean (two passes). */
+void orc_moments(const double *theta, const uint64_t *idx, uint64_t k,
+                 double mean[3], double var[3]) {
+  for (int j = 0; j < 3; ++j) {
+    if (k == 0) {
+      mean[j] = NAN;
+      var[j] = NAN;
+      continue;
+    }
+    double s = 0.0;
+    for (uint64_t t = 0; t < k; ++t) s += theta[3 * idx[t] + j];
+    mean[j] = s / (double)k;
+    if (k < 2) {
+      var[j] = NAN;
+      continue;
+    }
+    double q = 0.0;
+    for (uint64_t t = 0; t < k; ++t) {
+      double r = theta[3 * idx[t] + j] - mean[j];
+      q += r * r;
+    }
+    var[j] = q / (double)(k - 1);
+  }
+}
+
+/* ---------------------------------------------------------------------------
+ * Prior-predictive p-value (Sec. 4.1, Eq. 6 and Eq. 8) for the conjugate
+ * normal model y_i ~ N(mu, 1), mu ~ N(0, lambda^2).  The sufficient statistic
+ * ybar has prior predictive density N(0, lambda^2 + 1/n), which decreases in
+ * |ybar|, so the event pi(D) <= pi(D_obs) is |ybar| >= |ybar_obs|.  The
+ * probability is estimated by the indicator count of Algorithm 2's inner
+ * loop over M prior-predictive data sets.
+ * ------------------------------------------------------------------------- */
+typedef struct pv_job {
+  const double *lambda;
+  uint32_t n_lambda, n_obs;
+  uint64_t m_sets, lo, hi; /* flat range over (k, m) */
+  double ybar_obs;
+  uint32_t key[2];
+  uint64_t *counts; /* [n_lambda], private to the worker */
+  double *ybar;
+} pv_job;
+
+static void *pv_worker(void *arg) {
+  pv_job *J = (pv_job *)arg;
+  double *z = (double *)malloc(((size_t)J->n_obs + 4) * sizeof(double));
+  for (uint64_t f = J->lo; f < J->hi; ++f) {
+    uint32_t k = (uint32_t)(f / J->m_sets);
+    uint64_t m = f % J->m_sets;
+    /* normals 0..n of stream (seed, m, k, PATH) */
+    for (uint32_t t = 0; t <= J->n_obs; ++t) {
+      double zb[4];
+      block_normals(J->key, t / 4, (uint32_t)m, k, ORC_TAG_PATH, zb);
+      z[t] = zb[t % 4];
+    }
+    double mu = J->lambda[k] * z[0];
+    double s = 0.0;
+    for (uint32_t t = 1; t <= J->n_obs; ++t) s += z[t];
+    double ybar = mu + s / (double)J->n_obs;
+    if (J->ybar) J->ybar[f] = ybar;
+    if (fabs(ybar) >= fabs(J->ybar_obs)) J->counts[k] += 1;
+  }
+  free(z);
+  return NULL;
+}
+
+int orc_pvalue_sweep(const double *lambda, uint32_t n_lambda, uint32_t n_obs,
+                     uint64_t m_sets, double ybar_obs, uint64_t seed,
+                     uint64_t *counts, double *p, double *ybar, int n_threads) {
+  if (!lambda || !counts || n_lambda == 0 || n_obs == 0 || m_sets == 0) return -1;
+  if (m_sets > 0x100000000ull) return -1;
+  uint64_t total = (uint64_t)n_lambda * m_sets;
+  if (n_threads < 1) n_threads = 1;
+  if ((uint64_t)n_threads > total) n_threads = (int)total;
+  pv_job *jobs = (pv_job *)calloc((size_t)n_threads, sizeof(pv_job));
+  pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+  uint64_t *priv = (uint64_t *)calloc((size_t)n_threads * n_lambda, sizeof(uint64_t));
+  if (!jobs || !th || !priv) {
+    free(jobs);
+    free(th);
+    free(priv);
+    return -1;
+  }
+  for (int t = 0; t < n_threads; ++t) {
+    pv_job *J = &jobs[t];
+    J->lambda = lambda;
+    J->n_lambda = n_lambda;
+    J->n_obs = n_obs;
+    J->m_sets = m_sets;
+    J->lo = total * (uint64_t)t / (uint64_t)n_threads;
+    J->hi = total * (uint64_t)(t + 1) / (uint64_t)n_threads;
+    J->ybar_obs = ybar_obs;
+    seed_to_key(seed, J->key);
+    J->counts = priv + (size_t)t * n_lambda;
+    J->ybar = ybar;
+  }
+  for (int t = 1; t < n_threads; ++t) pthread_create(&th[t], NULL, pv_worker, &jobs[t]);
+  pv_worker(&jobs[0]);
+  for (int t = 1; t < n_threads; ++t) pthread_join(th[t], NULL);
+  for (uint32_t k = 0; k < n_lambda; ++k) {
+    uint64_t c = 0;
+    for (int t = 0; t < n_threads; ++t) c += priv[(size_t)t * n_lambda + k];
+    counts[k] = c;
+    if (p) p[k] = (double)c / (double)m_sets;
+  }
+  free(jobs);
+  free(th);
+  free(priv);
+  return 0;
+}
