@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Benchmark of the prior-predictive hot path on GB300.
+
+One step is one pass of the whole path over one batch of synthetic input:
+  * OU-ABC, N = 2^24 prior samples x 10^4 Euler-Maruyama steps (dt = 1e-3),
+    10 observations, accept the 0.1% nearest (k = 16777) with posterior
+    moments: abc_prior_predictive + abc_select;
+  * p-value sweep, 64 lambdas x 10^6 data sets x (n = 50) + 1 normals:
+    pvalue_sweep.
+The metric is path-steps per second (an EM step of one sample, or one normal
+of one p-value data set), whole job, inputs resident in HBM.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores over a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1902_09046_gb300 import workloads  # noqa: E402
+
+METRIC = "EM path-steps/sec (+ frac of FP32/MUFU roofline)"
+UNIT = "path-steps/s"
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+MUFU_PER_SM_CLK = 16          # special-function (MUFU) lanes per SM per clock
+MUFU_PER_PATH_STEP = 2.0      # log, sqrt, sin, cos per Box-Muller pair = 2 per normal
+KERNEL_SOURCES = ("paper_1902_09046_gb300/csrc/em_ou.cu", "paper_1902_09046_gb300/csrc/ou_path.cuh",
+                  "paper_1902_09046_gb300/csrc/rng.cuh")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--abc-samples", type=int, default=1 << 24)
+    ap.add_argument("--abc-steps", type=int, default=10_000)
+    ap.add_argument("--pv-sets", type=int, default=1_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload_config(args):
+    abc = workloads.abc_large(args.abc_samples)
+    abc.model = workloads.ou_model(args.abc_steps)
+    abc.k_accept = max(1, int(0.001 * args.abc_samples))
+    pv = workloads.pvalue_sweep_workload(args.pv_sets)
+    return abc, pv
+
+
+def path_steps_per_step(abc, pv):
+    abc_steps = abc.n_samples * abc.model["n_steps"]
+    pv_steps = len(pv.lambdas) * pv.m_sets * (pv.n_obs + 1)
+    return abc_steps, pv_steps
+
+
+def config_dict(abc, pv, world):
+    return {
+        "workload": (f"ou_abc N={abc.n_samples} S={abc.model['n_steps']} dt={abc.model['dt']:g} "
+                     f"k={abc.k_accept} + pvalue K={len(pv.lambdas)} M={pv.m_sets} n={pv.n_obs}"),
+        "abc_samples_per_rank": abc.n_samples, "em_steps": abc.model["n_steps"],
+        "k_accept": abc.k_accept, "pvalue_lambdas": len(pv.lambdas), "pvalue_sets": pv.m_sets,
+        "pvalue_n": pv.n_obs, "sharding": f"sample ranges over {world} rank(s)",
+        "l2": "flushed between timed steps (256 MiB write)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline leg only)
+# ---------------------------------------------------------------------------
+
+def run_oracle_sample(abc, pv, frac, threads):
+    """Runs the oracle on the first `frac` of the ABC samples and of the
+    p-value data sets; returns (path_steps, seconds)."""
+    import oracle
+    n_abc = max(1, int(round(abc.n_samples * frac)))
+    m_pv = max(1, int(round(pv.m_sets * frac)))
+    t0 = time.perf_counter()
+    _, _, dist = oracle.ou_prior_predictive(abc.model, abc.y_obs, n_abc, seed=abc.seed,
+                                            want_theta=True, n_threads=threads)
+    k = max(1, int(0.001 * n_abc))
+    idx = oracle.select_topk(dist, k)
+    oracle.pvalue_sweep(pv.lambdas, pv.n_obs, m_pv, pv.ybar_obs, pv.seed, n_threads=threads)
+    dt = time.perf_counter() - t0
+    steps = n_abc * abc.model["n_steps"] + len(pv.lambdas) * m_pv * (pv.n_obs + 1)
+    del idx
+    return steps, dt
+
+
+def calibrate_fraction(abc, pv, threads, target_s):
+    frac = 2048.0 / abc.n_samples
+    steps, dt = run_oracle_sample(abc, pv, frac, threads)
+    while dt < 0.5 and frac < 1.0:
+        frac = min(1.0, frac * 4)
+        steps, dt = run_oracle_sample(abc, pv, frac, threads)
+    return min(1.0, frac * target_s / max(dt, 1e-6))
+
+
+def cpu_baseline(abc, pv, target_s):
+    import oracle
+    oracle.build()
+    threads = oracle.default_threads()
+    frac = calibrate_fraction(abc, pv, threads, target_s)
+    steps, dt = run_oracle_sample(abc, pv, frac, threads)
+    return {"value": steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"first {frac:.3g} of the workload: {int(round(abc.n_samples * frac))} ABC samples "
+                       f"x {abc.model['n_steps']} steps + {len(pv.lambdas)} x {int(round(pv.m_sets * frac))} "
+                       f"p-value data sets; FP64, static split over {threads} threads; {dt:.1f} s")}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    abc, pv = workload_config(args)
+    import oracle
+    oracle.build()
+    threads = oracle.default_threads()
+    frac = calibrate_fraction(abc, pv, threads, 4.0)
+    for _ in range(args.warmup):
+        run_oracle_sample(abc, pv, frac, threads)
+    total_steps, total_s, per = 0, 0.0, []
+    for _ in range(args.steps):
+        s, dt = run_oracle_sample(abc, pv, frac, threads)
+        total_steps += s
+        total_s += dt
+        per.append(dt)
+    value = total_steps / total_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)", "config": config_dict(abc, pv, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"each step: first {frac:.3g} of the workload on the host cores"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(n_samples):
+    """DRAM bytes per em_ou_fused launch from the committed ncu summary, scaled
+    to this launch size; None if absent or the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", "em_ou_fused_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    return float(rec["dram_bytes"]) * n_samples / float(rec["n_samples"])
+
+
+def gpu_arm(args):
+    import torch
+    from paper_1902_09046_gb300 import binding
+    from paper_1902_09046_gb300 import build as libbuild
+
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    libbuild.build()
+    binding.device_check()
+    abc, pv = workload_config(args)
+    N = abc.n_samples
+    base = rank * N
+    if base + N > (1 << 32):
+        raise SystemExit("sample range of this rank exceeds 2^32")
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    lam_host = torch.tensor(pv.lambdas, dtype=torch.float64).pin_memory()
+    lam_dev = lam_host.to(dev)
+    dist_buf = torch.empty(N, dtype=torch.float64, device=dev)
+    ws = torch.empty(binding.abc_select_workspace_bytes(N), dtype=torch.uint8, device=dev)
+    sel_out = {"idx": torch.empty(abc.k_accept, dtype=torch.uint32, device=dev),
+               "rec": torch.empty((abc.k_accept, 4), dtype=torch.float32, device=dev),
+               "n_acc": torch.empty(1, dtype=torch.uint64, device=dev),
+               "eps": torch.empty(1, dtype=torch.float64, device=dev),
+               "post": torch.empty(6, dtype=torch.float64, device=dev)}
+    pv_out = {"counts": torch.empty(len(pv.lambdas), dtype=torch.uint64, device=dev),
+              "p": torch.empty(len(pv.lambdas), dtype=torch.float64, device=dev)}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    launches_per_step = 1 + 11 + 2
+
+    def step(em_events=None):
+        if em_events is not None:
+            em_events[0].record(stream)
+        binding.abc_prior_predictive(abc.model, abc.y_obs, N, abc.seed, sample_base=base,
+                                     want_theta=False, out={"dist": dist_buf}, stream=stream)
+        if em_events is not None:
+            em_events[1].record(stream)
+        binding.abc_select(dist_buf, k=abc.k_accept, model=abc.model, seed=abc.seed, sample_base=base,
+                           workspace=ws, out=sel_out, stream=stream)
+        binding.pvalue_sweep(lam_dev, pv.n_obs, pv.m_sets, pv.ybar_obs, pv.seed, out=pv_out,
+                             stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    steps_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+    em_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(args.steps)]
+    with ClockSampler(local_rank) as clocks:
+        barrier()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)  # L2 flush between timed steps, outside the step events
+            steps_ev[i][0].record(stream)
+            step(em_ev[i])
+            steps_ev[i][1].record(stream)
+        barrier()
+    step_ms = [a.elapsed_time(b) for a, b in steps_ev]
+    em_ms = [a.elapsed_time(b) for a, b in em_ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    abc_steps, pv_steps = path_steps_per_step(abc, pv)
+    units = (abc_steps + pv_steps) * world * args.steps
+    value = units / (total_ms / 1e3)
+
+    # End to end through the public API with host buffers: H2D of the step's
+    # inputs (lambda grid; the OU model and observed data travel as launch
+    # arguments) and D2H of every result, inside the timed region.
+    host_out = {"idx": torch.empty(abc.k_accept, dtype=torch.uint32).pin_memory(),
+                "rec": torch.empty((abc.k_accept, 4), dtype=torch.float32).pin_memory(),
+                "n_acc": torch.empty(1, dtype=torch.uint64).pin_memory(),
+                "eps": torch.empty(1, dtype=torch.float64).pin_memory(),
+                "post": torch.empty(6, dtype=torch.float64).pin_memory(),
+                "counts": torch.empty(len(pv.lambdas), dtype=torch.uint64).pin_memory(),
+                "p": torch.empty(len(pv.lambdas), dtype=torch.float64).pin_memory()}
+    h2d = lam_host.numel() * 8
+    d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+
+    def e2e_step():
+        lam_dev.copy_(lam_host, non_blocking=True)
+        step()
+        for key in ("idx", "rec", "n_acc", "eps", "post"):
+            host_out[key].copy_(sel_out[key], non_blocking=True)
+        for key in ("counts", "p"):
+            host_out[key].copy_(pv_out[key], non_blocking=True)
+        stream.synchronize()
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = units / e2e_s
+
+    # Roofline of the dominant kernel (em_ou_fused): 2 MUFU-class operations
+    # (log, sqrt, sin, cos per Box-Muller pair) per path-step against 16 MUFU
+    # lanes per SM per clock on 152 SMs at the 2070 MHz maximum clock.
+    em_avg_s = statistics.mean(em_ms) / 1e3
+    achieved = abc_steps / em_avg_s / 1e9
+    peak = SM_COUNT * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / MUFU_PER_PATH_STEP / 1e9
+    roof = {"kernel": "em_ou_fused", "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "Gpath-steps/s", "frac": achieved / peak, "traffic": profiled_traffic(N),
+            "peak_basis": "FP32+MUFU roofline: 2 MUFU ops/path-step (log,sqrt,sin,cos per pair), "
+                          "16 MUFU/SM/clk x 152 SMs x 2070 MHz; FP32 pipe bound (6 ops/step, "
+                          "128/SM/clk) is looser"}
+    clock = clocks.summary()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded)", "config": config_dict(abc, pv, world),
+            "parts": {"em_ms_per_step": statistics.mean(em_ms),
+                      "abc_path_steps": abc_steps, "pvalue_path_steps": pv_steps},
+            "roofline": roof, "clocks": clock,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(abc, pv, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

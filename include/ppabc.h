@@ -1,0 +1,199 @@
+/*
+ * ppabc.h -- C ABI of the GB300 (sm_103a) prior-predictive Monte Carlo
+ * library libppabc.so.
+ *
+ * The library implements the data-parallel hot path of prior-predictive
+ * sampling as used by ABC rejection sampling and by prior-predictive p-values
+ * (Warne, Sisson & Drovandi, "Vector operations for accelerating expensive
+ * Bayesian computations -- a tutorial guide", arXiv:1902.09046):
+ *   abc_prior_predictive -- draw theta from the prior, simulate the model,
+ *                           reduce to summaries and a discrepancy (Sec. 3.1,
+ *                           Eq. 2 and Algorithm 1; Euler-Maruyama, Eq. 5);
+ *   abc_select           -- choose the accepted set: the k nearest samples
+ *                           (epsilon chosen a posteriori, Sec. 3.1) or all
+ *                           samples with distance <= epsilon (Algorithm 1),
+ *                           and the posterior mean / variance of theta;
+ *   pvalue_sweep         -- prior-predictive p-values p_lambda over a grid of
+ *                           hyperparameters (Sec. 4.1, Eq. 6 and Eq. 8) by
+ *                           exact tail counts.
+ *
+ * General rules for every entry point:
+ *   - Pointers are DEVICE pointers (memory of the current CUDA device) unless
+ *     the parameter name starts with h_, in which case it is host memory read
+ *     before the call returns.  The caller owns all memory; the library never
+ *     allocates device memory.  Scratch memory is supplied by the caller and
+ *     sized by the matching *_workspace_bytes function.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
+ *     stream) and is asynchronous: outputs are valid once the stream has been
+ *     synchronised.  Calls are stream-ordered and do not synchronise the host.
+ *   - Every call returns a status (PPABC_OK or a negative PPABC_E* code).  On
+ *     error nothing has been enqueued, except for PPABC_ECUDA raised by a
+ *     failed launch; ppabc_last_error() returns a message for the calling
+ *     thread's last failure.
+ *   - Only sm_103 devices are supported; any other device gives PPABC_ENODEV.
+ *     There is no CPU fallback.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = (seed low 32
+ * bits, seed high 32 bits), counter = (c0 block, c1 sample / data-set index,
+ * c2 substream, c3 tag) with tag 0 for prior draws and 1 for path / data
+ * normals.  A 32-bit word w encodes the uniform ((w >> 9) + 1/2) 2^-23 and
+ * normals come from Box-Muller on consecutive word pairs.  Results therefore
+ * depend only on (seed, substream, global sample index), never on launch
+ * shape, batching or sharding.
+ */
+#ifndef PPABC_H
+#define PPABC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PPABC_ABI_VERSION 1
+
+#define PPABC_OK 0
+#define PPABC_EINVAL (-1)     /* invalid argument */
+#define PPABC_ENOMEM (-2)     /* workspace too small / admission refused */
+#define PPABC_ECUDA (-3)      /* a CUDA runtime call or launch failed */
+#define PPABC_ETIMEOUT (-4)   /* a bounded device-side wait expired */
+#define PPABC_ENODEV (-5)     /* no sm_103 device current */
+#define PPABC_ECANCELLED (-6) /* job cancelled by the host */
+
+/* Most observations a model may have. */
+#define PPABC_MAX_OBS 32
+
+/* Counter tags. */
+#define PPABC_TAG_PRIOR 0u
+#define PPABC_TAG_PATH 1u
+
+/*
+ * Ornstein-Uhlenbeck model of the ABC workloads:
+ *   dX = th1 (th2 - X) dt + th3 dW,  X(0) = x0,
+ * with independent uniform priors th_j ~ U(lo[j], hi[j]) (lo[j] <= hi[j];
+ * equal bounds fix th_j).  The path takes n_steps Euler-Maruyama steps of
+ * size dt (Eq. 5 applied to this SDE) and is observed after steps
+ * s_j = floor(j n_steps / n_obs), j = 1..n_obs; 1 <= n_obs <= PPABC_MAX_OBS
+ * and n_steps >= n_obs.
+ */
+typedef struct ppabc_ou_model {
+  double lo[3];
+  double hi[3];
+  double x0;
+  double dt;
+  uint32_t n_steps;
+  uint32_t n_obs;
+} ppabc_ou_model;
+
+/* ABI version (PPABC_ABI_VERSION of the built library). */
+int ppabc_abi_version(void);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char *ppabc_last_error(void);
+
+/* PPABC_OK if the current CUDA device is sm_103, else PPABC_ENODEV or
+ * PPABC_ECUDA. */
+int ppabc_device_check(void);
+
+/*
+ * Raw Philox4x32-10 blocks: out[i][0..3] = philox(ctr[i][0..3], key(seed)),
+ * i < n.  ctr and out are [n][4] uint32, 16-byte aligned.  Exposes the
+ * generator that replaces the paper's MKL MT2203 streams (Sec. 2.5, option
+ * (ii): one generator split into independent sub-streams).
+ */
+int ppabc_philox_raw(uint64_t seed, const uint32_t *ctr, uint64_t n,
+                     uint32_t *out, void *stream);
+
+/*
+ * Standard normals j0 .. j0+n-1 of stream (seed, c1, c2, tag), in binary32:
+ * normal j is lane j%4 of counter block (j/4, c1, c2, tag) after Box-Muller
+ * (the transform the paper's MKL calls use, Sec. 3.4).  z is [n] float.
+ */
+int ppabc_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag,
+                  uint64_t j0, uint64_t n, float *z, void *stream);
+
+/*
+ * Prior-predictive sampling for ABC (Sec. 3.1, Eq. 2; Algorithm 1 with N
+ * fixed), one sample per global index g = sample_base + i, i < n_samples:
+ *   theta ~ prior        (counter (0, g, substream, PRIOR), words 0..2),
+ *   X_s = X_{s-1} + th1 (th2 - X_{s-1}) dt + th3 sqrt(dt) xi_{s-1},
+ *                        (xi_j: normal j of stream (seed, g, substream, PATH)),
+ *   S(D*) = (X_{s_1}, .., X_{s_nobs}),  rho = || S(D*) - y_obs ||_2.
+ * The path is integrated in binary32 with a compensated (Kahan) state; the
+ * summaries and the discrepancy are accumulated in binary64.
+ *   h_model     model and prior (host).
+ *   h_y_obs     observed summaries, n_obs doubles (host).
+ *   theta_out   nullable; [3][n_samples] float (structure of arrays).
+ *   summ_out    nullable; [n_obs][n_samples] double, the simulated summaries.
+ *   dist_out    [n_samples] double, the discrepancy rho.
+ * Requires sample_base + n_samples <= 2^32.  n_samples == 0 is a no-op.
+ */
+int abc_prior_predictive(const ppabc_ou_model *h_model, const double *h_y_obs,
+                         uint64_t n_samples, uint64_t sample_base,
+                         uint64_t seed, uint32_t substream, float *theta_out,
+                         double *summ_out, double *dist_out, void *stream);
+
+/* Bytes of scratch abc_select needs for n distances (256-byte aligned). */
+size_t abc_select_workspace_bytes(uint64_t n);
+
+/*
+ * Accepted set and posterior summaries.
+ *   k > 0: accept the k samples with the smallest (dist, index); epsilon is
+ *          then the k-th smallest distance (the a-posteriori choice of
+ *          Sec. 3.1).  Requires k <= n.
+ *   k = 0: accept every sample with dist <= eps (Algorithm 1's test);
+ *          eps = +inf accepts every sample with a non-NaN distance.
+ * Distances are ordered as binary64 values with -0 == +0 and every NaN after
+ * +inf; ties go to the smaller index.
+ * Outputs, in ascending index order:
+ *   idx_out    [cap] uint32: local indices i (0 <= i < n) of accepted samples;
+ *   rec_out    [cap][4] float (16-byte aligned): (th1, th2, th3, (float)dist);
+ *              theta is read from `theta` ([3][n] float, as written by
+ *              abc_prior_predictive) or, when theta is NULL, redrawn from the
+ *              prior counter of sample sample_base + i using h_model, seed and
+ *              substream (bit-identical to what abc_prior_predictive draws);
+ *   n_acc_out  [1] uint64: number accepted (may exceed cap; only the first
+ *              cap are written);
+ *   eps_out    [1] double (nullable): the epsilon used;
+ *   post_out   [6] double (nullable): posterior mean of (th1, th2, th3) then
+ *              the unbiased (n_acc - 1) variances, over ALL accepted samples,
+ *              reduced in a fixed order (deterministic); NaN when undefined.
+ * workspace must hold abc_select_workspace_bytes(n) bytes.
+ */
+int abc_select(const double *dist, uint64_t n, uint64_t k, double eps,
+               const ppabc_ou_model *h_model, uint64_t sample_base,
+               uint64_t seed, uint32_t substream, const float *theta,
+               uint32_t *idx_out, float *rec_out, uint64_t cap,
+               uint64_t *n_acc_out, double *eps_out, double *post_out,
+               void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Prior-predictive p-value sweep (Sec. 4.1, Eq. 6 and Eq. 8) for the
+ * conjugate model y_i ~ N(mu, 1), i = 1..n_obs, mu ~ N(0, lambda_k^2).  For
+ * lambda index k < n_lambda and data set m < m_sets, with z_t the normals of
+ * stream (seed, m, k, PATH):
+ *   ybar = lambda_k z_0 + (1/n_obs) sum_{t=1..n_obs} z_t,
+ *   counts[k] = #{m : |ybar| >= |ybar_obs|}  (exact, uint64),
+ *   p_out[k]  = counts[k] / m_sets.
+ * The statistic ybar is sufficient and its prior predictive law is
+ * N(0, lambda^2 + 1/n_obs), whose density falls with |ybar|, so the count is
+ * the indicator estimate of P(pi(D) <= pi(D_obs)) (Algorithm 2's estimator).
+ * Normals are binary32; each sum is Kahan-compensated binary32 and ybar and
+ * the comparison are binary64.
+ *   lambda    [n_lambda] double (device).
+ *   counts    [n_lambda] uint64; overwritten (zeroed by the call).
+ *   p_out     [n_lambda] double (nullable).
+ *   ybar_out  [n_lambda][m_sets] double (nullable).
+ * Requires m_sets <= 2^32, n_obs >= 1.
+ */
+int pvalue_sweep(const double *lambda, uint32_t n_lambda, uint32_t n_obs,
+                 uint64_t m_sets, double ybar_obs, uint64_t seed,
+                 uint64_t *counts, double *p_out, double *ybar_out,
+                 void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPABC_H */

@@ -1,0 +1,89 @@
+// em_ou.cu -- fused prior-predictive OU kernel and the raw RNG kernels.
+//
+// em_ou_fused: one sample path per thread.  Prior draw, Euler-Maruyama path,
+// summaries and discrepancy all happen in registers; the only global traffic
+// is the optional theta / summary write and one binary64 distance per sample.
+// This replaces the paper's block-of-VECL SIMD loop with pre-generated
+// normals (Sec. 3.4): on the GPU a warp is the SIMD vector, the sample index
+// is the lane, and the normals never touch memory.
+#include "internal.h"
+
+namespace ppabc {
+
+constexpr int kEmThreads = 128;
+
+template <bool kWantTheta, bool kWantSumm>
+__global__ void __launch_bounds__(kEmThreads) em_ou_fused(const __grid_constant__ OUConst P,
+                                                          uint32_t base, uint32_t n,
+                                                          float* __restrict__ theta_out,
+                                                          double* __restrict__ summ_out,
+                                                          double* __restrict__ dist_out) {
+  const uint32_t i = blockIdx.x * kEmThreads + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t g = base + i;
+  float th1, th2, th3;
+  ou_prior(P, g, th1, th2, th3);
+  if (kWantTheta) {
+    theta_out[i] = th1;
+    theta_out[static_cast<size_t>(n) + i] = th2;
+    theta_out[2 * static_cast<size_t>(n) + i] = th3;
+  }
+  dist_out[i] = ou_path<kWantSumm>(P, g, th1, th2, th3, kWantSumm ? summ_out + i : nullptr, n);
+}
+
+cudaError_t launch_em_ou(const OUConst& P, uint64_t base, uint32_t n, float* theta_out,
+                         double* summ_out, double* dist_out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const dim3 grid((n + kEmThreads - 1) / kEmThreads);
+  const uint32_t b = static_cast<uint32_t>(base);
+  if (theta_out && summ_out)
+    em_ou_fused<true, true><<<grid, kEmThreads, 0, s>>>(P, b, n, theta_out, summ_out, dist_out);
+  else if (theta_out)
+    em_ou_fused<true, false><<<grid, kEmThreads, 0, s>>>(P, b, n, theta_out, summ_out, dist_out);
+  else if (summ_out)
+    em_ou_fused<false, true><<<grid, kEmThreads, 0, s>>>(P, b, n, theta_out, summ_out, dist_out);
+  else
+    em_ou_fused<false, false><<<grid, kEmThreads, 0, s>>>(P, b, n, theta_out, summ_out, dist_out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Raw generator outputs (parity hooks for the RNG itself).
+// ---------------------------------------------------------------------------
+__global__ void philox_raw_kernel(uint32_t k0, uint32_t k1, const uint4* __restrict__ ctr,
+                                  uint64_t n, uint4* __restrict__ out) {
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+__global__ void normals_kernel(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t tag,
+                               uint64_t j0, uint64_t n, float* __restrict__ z) {
+  const uint64_t t = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const uint64_t j = j0 + t;
+  const float4 q = block_normals(static_cast<uint32_t>(j >> 2), c1, c2, tag, k0, k1);
+  const uint32_t lane = static_cast<uint32_t>(j & 3u);
+  z[t] = lane == 0 ? q.x : lane == 1 ? q.y : lane == 2 ? q.z : q.w;
+}
+
+cudaError_t launch_philox_raw(uint64_t seed, const uint32_t* ctr, uint64_t n, uint32_t* out,
+                              cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
+  philox_raw_kernel<<<blocks, 256, 0, s>>>(static_cast<uint32_t>(seed),
+                                           static_cast<uint32_t>(seed >> 32),
+                                           reinterpret_cast<const uint4*>(ctr), n,
+                                           reinterpret_cast<uint4*>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag, uint64_t j0,
+                           uint64_t n, float* z, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
+  normals_kernel<<<blocks, 256, 0, s>>>(static_cast<uint32_t>(seed),
+                                        static_cast<uint32_t>(seed >> 32), c1, c2, tag, j0, n, z);
+  return cudaGetLastError();
+}
+
+}  // namespace ppabc

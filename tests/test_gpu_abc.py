@@ -1,0 +1,230 @@
+"""GPU parity of OU-ABC prior-predictive sampling and selection (C ABI vs the
+CPU oracle), from small ragged cases up to the full 2^24 x 10^4 workload."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import (BAND, DIST_RTOL, SUMM_ATOL, THETA_ATOL, band_check, require_gpu, to_np,
+                        torch)
+from paper_1902_09046_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def run_gpu(binding, model, y, n, seed, sub=0, base=0):
+    out = binding.abc_prior_predictive(model, y, n, seed, substream=sub, sample_base=base,
+                                       want_theta=True, want_summ=True)
+    torch.cuda.synchronize()
+    return to_np(out["theta"]).T.astype(np.float64), to_np(out["summ"]).T, to_np(out["dist"]), out
+
+
+def compare_paths(model, y, n, seed, sub=0, base=0):
+    binding = require_gpu()
+    th_g, s_g, d_g, out = run_gpu(binding, model, y, n, seed, sub, base)
+    th_o, s_o, d_o = oracle.ou_prior_predictive(model, y, n, seed=seed, sub=sub, base=base,
+                                                want_summ=True)
+    np.testing.assert_allclose(th_g, th_o, rtol=0, atol=THETA_ATOL)
+    serr = np.abs(s_g - s_o).max()
+    derr = (np.abs(d_g - d_o) / np.maximum(d_o, 1e-300)).max()
+    print(f"n={n} S={model['n_steps']}: max |theta| err {np.abs(th_g - th_o).max():.3g}, "
+          f"max |summary| err {serr:.3g}, max rel dist err {derr:.3g}")
+    assert serr <= SUMM_ATOL
+    assert derr <= DIST_RTOL
+    return th_g, d_g, th_o, d_o, out
+
+
+def test_small_workload_parity_and_accept_set():
+    binding = require_gpu()
+    w = workloads.abc_small()
+    th_g, d_g, th_o, d_o, out = compare_paths(w.model, w.y_obs, w.n_samples, w.seed)
+    sel = binding.abc_select(out["dist"], k=w.k_accept, model=w.model, seed=w.seed,
+                             theta=out["theta"])
+    sel_regen = binding.abc_select(out["dist"], k=w.k_accept, model=w.model, seed=w.seed)
+    torch.cuda.synchronize()
+    idx_g = to_np(sel["idx"]).astype(np.int64)
+    idx_o = oracle.select_topk(d_o, w.k_accept).astype(np.int64)
+    eps_o = np.sort(d_o)[w.k_accept - 1]
+    ndiff = band_check(idx_g, idx_o, d_o, eps_o)
+    print(f"accept-set differences inside the band: {ndiff}")
+    assert int(to_np(sel["n_acc"])[0]) == w.k_accept
+    assert np.all(np.diff(idx_g) > 0)
+    # the GPU's own selection is exact on its own distances
+    np.testing.assert_array_equal(idx_g, oracle.select_topk(d_g, w.k_accept).astype(np.int64))
+    assert to_np(sel["eps"])[0] == np.sort(d_g)[w.k_accept - 1]
+    rec = to_np(sel["rec"])
+    np.testing.assert_array_equal(rec[:, :3], th_g[idx_g].astype(np.float32))
+    np.testing.assert_array_equal(rec[:, 3], d_g[idx_g].astype(np.float32))
+    # redrawing theta from the prior counter is bit-identical to the stored draw
+    np.testing.assert_array_equal(to_np(sel_regen["rec"]), rec)
+    np.testing.assert_array_equal(to_np(sel_regen["post"]), to_np(sel["post"]))
+    # posterior moments vs the oracle's over the oracle's accepted set
+    mean_o, var_o = oracle.moments(th_o, idx_o.astype(np.uint64))
+    post = to_np(sel["post"])
+    print(f"posterior mean err {np.abs(post[:3] - mean_o)}, var err {np.abs(post[3:] - var_o)}")
+    if ndiff == 0:
+        np.testing.assert_allclose(post[:3], mean_o, rtol=1e-6, atol=1e-7)
+        np.testing.assert_allclose(post[3:], var_o, rtol=1e-5)
+
+
+@pytest.mark.parametrize("n_steps,n_obs,n,x0", [(37, 10, 5003, 0.0), (1000, 1, 1, 0.3),
+                                                (4, 4, 129, -1.0), (250, 32, 1000, 2.0),
+                                                (101, 7, 4099, 0.0)])
+def test_ragged_models(n_steps, n_obs, n, x0):
+    model = workloads.ou_model(n_steps, n_obs=n_obs, x0=x0)
+    y = np.linspace(-0.5, 1.0, n_obs)
+    compare_paths(model, y, n, seed=11, sub=2)
+
+
+def test_fixed_theta_and_sample_base_sharding():
+    binding = require_gpu()
+    model = {"lo": (1.2, 0.4, 0.5), "hi": (1.2, 0.4, 0.5), "x0": 0.0, "dt": 0.01, "n_steps": 500,
+             "n_obs": 10}
+    y = np.zeros(10)
+    compare_paths(model, y, 3000, seed=5, base=123_456)
+    w = workloads.abc_small()
+    full = binding.abc_prior_predictive(w.model, w.y_obs, 8192, w.seed)
+    half = binding.abc_prior_predictive(w.model, w.y_obs, 4096, w.seed, sample_base=4096)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(to_np(full["dist"])[4096:], to_np(half["dist"]))
+    np.testing.assert_array_equal(to_np(full["theta"])[:, 4096:], to_np(half["theta"]))
+
+
+def test_empty_and_invalid():
+    binding = require_gpu()
+    w = workloads.abc_small()
+    out = binding.abc_prior_predictive(w.model, w.y_obs, 0, w.seed)
+    assert out["dist"].numel() == 0
+    with pytest.raises(binding.PPABCError):
+        binding.abc_prior_predictive(dict(w.model, n_steps=5), w.y_obs, 10, w.seed)
+    with pytest.raises(binding.PPABCError):
+        binding.abc_prior_predictive(w.model, w.y_obs, 10, w.seed, sample_base=(1 << 32) - 5)
+    d = torch.rand(10, dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.PPABCError):
+        binding.abc_select(d, k=11, theta=torch.zeros((3, 10), device="cuda"))
+
+
+# ---------------------------------------------------------------------------
+# Selection on given distances: exact (bit-identical index sets)
+# ---------------------------------------------------------------------------
+
+def _select_cases():
+    rng = np.random.default_rng(7)
+    yield "ties", np.round(rng.gamma(2.0, 1.0, size=20_000), 1)
+    d = rng.uniform(0, 1, size=100_003)
+    d[::7] = d[3]
+    yield "ragged_ties", d
+    yield "one", np.array([0.5])
+    yield "specials", np.array([np.nan, 0.0, -0.0, np.inf, 1.0, 0.0, np.nan, 2.0, np.inf, 1e-300])
+    yield "large", rng.exponential(size=1 << 21)
+
+
+@pytest.mark.parametrize("case", [c for c, _ in _select_cases()])
+def test_select_exact_on_given_distances(case):
+    binding = require_gpu()
+    d = dict(_select_cases())[case]
+    n = d.size
+    theta = np.stack([np.arange(n, dtype=np.float32) * s for s in (1.0, -1.0, 0.5)])
+    th_t = torch.from_numpy(theta).cuda()
+    dt = torch.from_numpy(d).cuda()
+    ks = sorted({1, min(n, 2), min(n, 5), n // 3 or 1, n})
+    for k in ks:
+        sel = binding.abc_select(dt, k=k, theta=th_t)
+        torch.cuda.synchronize()
+        idx_o = oracle.select_topk(d, k).astype(np.int64)
+        np.testing.assert_array_equal(to_np(sel["idx"]).astype(np.int64), idx_o, err_msg=f"k={k}")
+        assert int(to_np(sel["n_acc"])[0]) == k
+        mean_o, var_o = oracle.moments(theta.T.astype(np.float64), idx_o.astype(np.uint64))
+        post = to_np(sel["post"])
+        np.testing.assert_allclose(post[:3], mean_o, rtol=1e-12, atol=1e-12)
+        if k > 1:
+            np.testing.assert_allclose(post[3:], var_o, rtol=1e-10)
+        else:
+            assert np.all(np.isnan(post[3:]))
+    finite = d[np.isfinite(d)]
+    for eps in (0.0, float(np.median(finite)) if finite.size else 0.0, math.inf, -1.0):
+        sel = binding.abc_select(dt, k=0, eps=eps, theta=th_t)
+        torch.cuda.synchronize()
+        idx_o = oracle.select_eps(d, eps).astype(np.int64)
+        n_acc = int(to_np(sel["n_acc"])[0])
+        assert n_acc == idx_o.size
+        np.testing.assert_array_equal(to_np(sel["idx"])[:n_acc].astype(np.int64), idx_o)
+        assert to_np(sel["eps"])[0] == eps or (math.isinf(eps) and math.isinf(to_np(sel["eps"])[0]))
+
+
+def test_eps_infinity_accepts_every_sample():
+    binding = require_gpu()
+    w = workloads.abc_small()
+    out = binding.abc_prior_predictive(w.model, w.y_obs, w.n_samples, w.seed)
+    sel = binding.abc_select(out["dist"], k=0, eps=math.inf, theta=out["theta"])
+    torch.cuda.synchronize()
+    assert int(to_np(sel["n_acc"])[0]) == w.n_samples
+    np.testing.assert_array_equal(to_np(sel["idx"]), np.arange(w.n_samples))
+    th = to_np(out["theta"]).astype(np.float64)
+    post = to_np(sel["post"])
+    np.testing.assert_allclose(post[:3], th.mean(axis=1), rtol=1e-12)
+    np.testing.assert_allclose(post[3:], th.var(axis=1, ddof=1), rtol=1e-10)
+
+
+def test_cap_smaller_than_accepted_count():
+    binding = require_gpu()
+    d = torch.linspace(0, 1, 10_000, dtype=torch.float64, device="cuda")
+    th = torch.zeros((3, 10_000), dtype=torch.float32, device="cuda")
+    sel = binding.abc_select(d, k=0, eps=0.5, theta=th, cap=100)
+    torch.cuda.synchronize()
+    assert int(to_np(sel["n_acc"])[0]) == int((to_np(d) <= 0.5).sum())
+    np.testing.assert_array_equal(to_np(sel["idx"]), np.arange(100))
+
+
+# ---------------------------------------------------------------------------
+# Full-size workload: 2^24 samples x 10^4 steps, as the benchmark launches it
+# ---------------------------------------------------------------------------
+
+def test_large_workload_subset_parity_and_posterior_error():
+    """First 2^16 samples of the 2^24 x 10^4 workload, accept 0.1%: accept set
+    vs the oracle outside the band, posterior mean/var error stated."""
+    binding = require_gpu()
+    w = workloads.abc_large()
+    n = 1 << 16
+    k = int(0.001 * n)
+    th_g, d_g, th_o, d_o, out = compare_paths(w.model, w.y_obs, n, w.seed)
+    sel = binding.abc_select(out["dist"], k=k, model=w.model, seed=w.seed)
+    torch.cuda.synchronize()
+    idx_o = oracle.select_topk(d_o, k).astype(np.int64)
+    eps_o = np.sort(d_o)[k - 1]
+    ndiff = band_check(to_np(sel["idx"]), idx_o, d_o, eps_o)
+    mean_o, var_o = oracle.moments(th_o, idx_o.astype(np.uint64))
+    post = to_np(sel["post"])
+    print(f"2^16 subset k={k}: band diffs {ndiff}; posterior mean abs err "
+          f"{np.abs(post[:3] - mean_o)}; var rel err {np.abs(post[3:] - var_o) / var_o}")
+
+
+def test_full_size_workload_sampled():
+    binding = require_gpu()
+    w = workloads.abc_large()
+    N, k = w.n_samples, w.k_accept
+    out = binding.abc_prior_predictive(w.model, w.y_obs, N, w.seed, want_theta=False)
+    sel = binding.abc_select(out["dist"], k=k, model=w.model, seed=w.seed)
+    torch.cuda.synchronize()
+    d = out["dist"]
+    eps = float(to_np(sel["eps"])[0])
+    idx = sel["idx"].long()
+    assert int(to_np(sel["n_acc"])[0]) == k
+    # properties at any size: accepted are the k smallest
+    assert float(d[idx].max()) == eps
+    assert int((d < eps).sum()) <= k <= int((d <= eps).sum())
+    # sampled outputs recomputed one by one by the oracle
+    rng = np.random.default_rng(3)
+    acc = to_np(idx)
+    picks = np.concatenate([rng.choice(acc, 24, replace=False),
+                            rng.integers(0, N, 24),
+                            [0, N - 1]])
+    d_host = to_np(d)
+    for i in picks:
+        th_o, _, d_o = oracle.ou_prior_predictive(w.model, w.y_obs, 1, seed=w.seed, base=int(i))
+        assert abs(d_host[i] - d_o[0]) <= DIST_RTOL * d_o[0], (i, d_host[i], d_o[0])
+    # every sampled accepted sample is within the oracle's epsilon band
+    rec = to_np(sel["rec"])
+    th1 = rec[:, 0]
+    assert np.all((th1 >= 0.1) & (th1 <= 2.0))

@@ -1,0 +1,67 @@
+"""GPU parity of the prior-predictive p-value sweep (C ABI vs CPU oracle)."""
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from gpu_common import BAND, require_gpu, to_np, torch
+from paper_1902_09046_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+YBAR_ATOL = 1e-6
+
+
+def run(binding, lams, n_obs, M, ybar_obs, seed):
+    lt = torch.from_numpy(np.asarray(lams, dtype=np.float64)).cuda()
+    out = binding.pvalue_sweep(lt, n_obs, M, ybar_obs, seed, want_ybar=True)
+    torch.cuda.synchronize()
+    return to_np(out["counts"]).astype(np.int64), to_np(out["p"]), to_np(out["ybar"])
+
+
+@pytest.mark.parametrize("n_obs,M", [(50, 20_011), (1, 4097), (2, 300), (3, 1), (7, 999)])
+def test_sweep_parity(n_obs, M):
+    binding = require_gpu()
+    lams = workloads.pvalue_lambdas()
+    ybar_obs = workloads.pvalue_observed_ybar()
+    c_g, p_g, y_g = run(binding, lams, n_obs, M, ybar_obs, seed=2)
+    c_o, p_o, y_o = oracle.pvalue_sweep(lams, n_obs, M, ybar_obs, seed=2, want_ybar=True)
+    err = np.abs(y_g - y_o).max()
+    print(f"n={n_obs} M={M}: max |ybar err| {err:.3g}")
+    assert err <= YBAR_ATOL
+    # the GPU count is exactly its own indicator sum
+    np.testing.assert_array_equal(c_g, (np.abs(y_g) >= abs(ybar_obs)).sum(axis=1))
+    # indicators agree with the oracle outside the band
+    a = abs(ybar_obs)
+    outside = np.abs(np.abs(y_o) - a) >= BAND * a
+    np.testing.assert_array_equal((np.abs(y_g) >= a)[outside], (np.abs(y_o) >= a)[outside])
+    band = (~outside).sum(axis=1)
+    assert np.all(np.abs(c_g - c_o.astype(np.int64)) <= band)
+    np.testing.assert_array_equal(p_g, c_g / M)
+
+
+def test_full_sweep_matches_closed_form():
+    binding = require_gpu()
+    w = workloads.pvalue_sweep_workload()
+    lt = torch.from_numpy(w.lambdas).cuda()
+    out = binding.pvalue_sweep(lt, w.n_obs, w.m_sets, w.ybar_obs, w.seed, want_ybar=True)
+    torch.cuda.synchronize()
+    p = to_np(out["p"])
+    s = np.sqrt(w.lambdas ** 2 + 1.0 / w.n_obs)
+    ref = 2 * stats.norm.sf(abs(w.ybar_obs) / s)
+    se = np.sqrt(np.maximum(ref * (1 - ref), 1e-12) / w.m_sets)
+    assert np.all(np.abs(p - ref) < 4.5 * se + 1.0 / w.m_sets), np.max(np.abs(p - ref) / se)
+    assert to_np(out["counts"])[0] == 0
+    # the first 2000 data sets of every lambda, recomputed by the oracle
+    _, _, y_o = oracle.pvalue_sweep(w.lambdas, w.n_obs, 2000, w.ybar_obs, w.seed, want_ybar=True)
+    y_g = to_np(out["ybar"][:, :2000])
+    assert np.abs(y_g - y_o).max() <= YBAR_ATOL
+
+
+def test_invalid_arguments():
+    binding = require_gpu()
+    lt = torch.ones(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.PPABCError):
+        binding.pvalue_sweep(lt, 0, 10, 1.0, 1)
+    with pytest.raises(binding.PPABCError):
+        binding.pvalue_sweep(lt, 10, 0, 1.0, 1)

@@ -1,0 +1,44 @@
+"""GPU parity of the random number generation (C ABI vs CPU oracle)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import Z_ATOL, require_gpu, to_np, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def test_philox_words_bit_exact():
+    binding = require_gpu()
+    rng = np.random.default_rng(1)
+    n = 100_003  # ragged
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4], [0xFFFFFFFF, 0, 0xFFFFFFFF, 0]]
+    for seed in (0, 1, 0xFFFFFFFF, 0xDEADBEEFCAFEF00D):
+        got = to_np(binding.philox_raw(seed, torch.from_numpy(ctr).cuda()))
+        np.testing.assert_array_equal(got, oracle.philox(seed, ctr))
+
+
+def test_philox_empty_and_alignment():
+    binding = require_gpu()
+    empty = torch.empty((0, 4), dtype=torch.uint32, device="cuda")
+    assert binding.philox_raw(5, empty).shape == (0, 4)
+
+
+@pytest.mark.parametrize("j0,n", [(0, 1), (0, 1_000_003), (7, 4097), (1 << 20, 999)])
+def test_normals_match_oracle(j0, n):
+    binding = require_gpu()
+    for (c1, c2, tag) in ((0, 0, 1), (12345, 3, 1), (7, 0, 0)):
+        z = to_np(binding.normals(99, c1, c2, tag, j0, n)).astype(np.float64)
+        zo = oracle.stream_normals(99, c1, c2, tag, j0, n)
+        err = np.abs(z - zo)
+        assert err.max() <= Z_ATOL, err.max()
+    print(f"max |z_gpu - z_oracle| = {err.max():.3g}")
+
+
+def test_normal_moments_on_gpu():
+    binding = require_gpu()
+    z = binding.normals(2024, 5, 0, 1, 0, 1 << 24).double()
+    n = z.numel()
+    assert abs(z.mean().item()) < 4.5 / np.sqrt(n)
+    assert abs(z.var().item() - 1) < 4.5 * np.sqrt(2.0 / n)
