@@ -68,11 +68,15 @@ def test_small_workload_parity_and_accept_set():
         np.testing.assert_allclose(post[3:], var_o, rtol=1e-5)
 
 
-@pytest.mark.parametrize("n_steps,n_obs,n,x0", [(37, 10, 5003, 0.0), (1000, 1, 1, 0.3),
-                                                (4, 4, 129, -1.0), (250, 32, 1000, 2.0),
-                                                (101, 7, 4099, 0.0)])
-def test_ragged_models(n_steps, n_obs, n, x0):
-    model = workloads.ou_model(n_steps, n_obs=n_obs, x0=x0)
+# (steps, observations, samples, x0, horizon): th1 dt stays below 1 so the
+# Euler-Maruyama recursion is stable for every prior draw.
+@pytest.mark.parametrize("n_steps,n_obs,n,x0,t_end", [(37, 10, 5003, 0.0, 10.0),
+                                                      (1000, 1, 1, 0.3, 10.0),
+                                                      (4, 4, 129, -1.0, 0.4),
+                                                      (250, 32, 1000, 2.0, 10.0),
+                                                      (101, 7, 4099, 0.0, 10.0)])
+def test_ragged_models(n_steps, n_obs, n, x0, t_end):
+    model = workloads.ou_model(n_steps, t_end=t_end, n_obs=n_obs, x0=x0)
     y = np.linspace(-0.5, 1.0, n_obs)
     compare_paths(model, y, n, seed=11, sub=2)
 
