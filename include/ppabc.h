@@ -171,11 +171,13 @@ int abc_select(const double *dist, uint64_t n, uint64_t k, double eps,
 /*
  * Prior-predictive p-value sweep (Sec. 4.1, Eq. 6 and Eq. 8) for the
  * conjugate model y_i ~ N(mu, 1), i = 1..n_obs, mu ~ N(0, lambda_k^2).  For
- * lambda index k < n_lambda and data set m < m_sets, with z_t the normals of
- * stream (seed, m, k, PATH):
+ * lambda index k < n_lambda and data set m = set_base .. set_base+m_sets-1,
+ * with z_t the normals of stream (seed, m, k, PATH):
  *   ybar = lambda_k z_0 + (1/n_obs) sum_{t=1..n_obs} z_t,
  *   counts[k] = #{m : |ybar| >= |ybar_obs|}  (exact, uint64),
  *   p_out[k]  = counts[k] / m_sets.
+ * set_base lets ranks of a sharded sweep take disjoint data-set ranges; the
+ * counts of all ranks then add up to the unsharded counts.
  * The statistic ybar is sufficient and its prior predictive law is
  * N(0, lambda^2 + 1/n_obs), whose density falls with |ybar|, so the count is
  * the indicator estimate of P(pi(D) <= pi(D_obs)) (Algorithm 2's estimator).
@@ -185,10 +187,10 @@ int abc_select(const double *dist, uint64_t n, uint64_t k, double eps,
  *   counts    [n_lambda] uint64; overwritten (zeroed by the call).
  *   p_out     [n_lambda] double (nullable).
  *   ybar_out  [n_lambda][m_sets] double (nullable).
- * Requires m_sets <= 2^32, n_obs >= 1.
+ * Requires 1 <= m_sets, set_base + m_sets <= 2^32, n_obs >= 1.
  */
 int pvalue_sweep(const double *lambda, uint32_t n_lambda, uint32_t n_obs,
-                 uint64_t m_sets, double ybar_obs, uint64_t seed,
+                 uint64_t m_sets, uint64_t set_base, double ybar_obs, uint64_t seed,
                  uint64_t *counts, double *p_out, double *ybar_out,
                  void *stream);
 

@@ -72,7 +72,7 @@ def _load():
             lib.orc_select_eps.restype = u64
             lib.orc_moments.argtypes = [P, P, u64, P, P]
             lib.orc_moments.restype = None
-            lib.orc_pvalue_sweep.argtypes = [P, u32, u32, u64, dbl, u64, P, P, P, i32]
+            lib.orc_pvalue_sweep.argtypes = [P, u32, u32, u64, u64, dbl, u64, P, P, P, i32]
             lib.orc_pvalue_sweep.restype = i32
             _lib = lib
     return _lib
@@ -158,14 +158,14 @@ def moments(theta: np.ndarray, idx: np.ndarray):
 
 
 def pvalue_sweep(lambdas, n_obs: int, m_sets: int, ybar_obs: float, seed: int,
-                 want_ybar: bool = False, n_threads: int | None = None):
+                 want_ybar: bool = False, n_threads: int | None = None, base: int = 0):
     """(counts [K] uint64, p [K], ybar [K,M] | None)."""
     lam = np.ascontiguousarray(lambdas, dtype=np.float64)
     K = lam.shape[0]
     counts = np.zeros(K, dtype=np.uint64)
     p = np.zeros(K, dtype=np.float64)
     ybar = np.zeros((K, m_sets), dtype=np.float64) if want_ybar else None
-    rc = _load().orc_pvalue_sweep(_ptr(lam), K, n_obs, m_sets, float(ybar_obs), seed,
+    rc = _load().orc_pvalue_sweep(_ptr(lam), K, n_obs, m_sets, base, float(ybar_obs), seed,
                                   _ptr(counts), _ptr(p), _ptr(ybar),
                                   n_threads or default_threads())
     if rc != 0:

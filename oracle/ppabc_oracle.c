@@ -311,7 +311,7 @@ void orc_moments(const double *theta, const uint64_t *idx, uint64_t k,
 typedef struct pv_job {
   const double *lambda;
   uint32_t n_lambda, n_obs;
-  uint64_t m_sets, lo, hi; /* flat range over (k, m) */
+  uint64_t m_sets, base, lo, hi; /* flat range over (k, m) */
   double ybar_obs;
   uint32_t key[2];
   uint64_t *counts; /* [n_lambda], private to the worker */
@@ -323,7 +323,7 @@ static void *pv_worker(void *arg) {
   double *z = (double *)malloc(((size_t)J->n_obs + 4) * sizeof(double));
   for (uint64_t f = J->lo; f < J->hi; ++f) {
     uint32_t k = (uint32_t)(f / J->m_sets);
-    uint64_t m = f % J->m_sets;
+    uint64_t m = J->base + f % J->m_sets;
     /* normals 0..n of stream (seed, m, k, PATH) */
     for (uint32_t t = 0; t <= J->n_obs; ++t) {
       double zb[4];
@@ -342,10 +342,10 @@ static void *pv_worker(void *arg) {
 }
 
 int orc_pvalue_sweep(const double *lambda, uint32_t n_lambda, uint32_t n_obs,
-                     uint64_t m_sets, double ybar_obs, uint64_t seed,
+                     uint64_t m_sets, uint64_t base, double ybar_obs, uint64_t seed,
                      uint64_t *counts, double *p, double *ybar, int n_threads) {
   if (!lambda || !counts || n_lambda == 0 || n_obs == 0 || m_sets == 0) return -1;
-  if (m_sets > 0x100000000ull) return -1;
+  if (m_sets > 0x100000000ull || base > 0x100000000ull - m_sets) return -1;
   uint64_t total = (uint64_t)n_lambda * m_sets;
   if (n_threads < 1) n_threads = 1;
   if ((uint64_t)n_threads > total) n_threads = (int)total;
@@ -364,6 +364,7 @@ int orc_pvalue_sweep(const double *lambda, uint32_t n_lambda, uint32_t n_obs,
     J->n_lambda = n_lambda;
     J->n_obs = n_obs;
     J->m_sets = m_sets;
+    J->base = base;
     J->lo = total * (uint64_t)t / (uint64_t)n_threads;
     J->hi = total * (uint64_t)(t + 1) / (uint64_t)n_threads;
     J->ybar_obs = ybar_obs;

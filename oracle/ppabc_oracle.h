@@ -81,12 +81,12 @@ void orc_moments(const double *theta, const uint64_t *idx, uint64_t k,
                  double mean[3], double var[3]);
 
 /* Prior-predictive p-value sweep for y_i ~ N(mu,1), i=1..n, mu ~ N(0,lam^2):
- * for each lambda_k and data set m = 0..M-1 the normals of stream
+ * for each lambda_k and data set m = base..base+M-1 the normals of stream
  * (seed, c1 = m, c2 = k, PATH) give mu = lam_k z_0 and
  * ybar = mu + (1/n) sum_{i=1..n} z_i; counts[k] = #{m : |ybar| >= |ybar_obs|},
  * p[k] = counts[k] / M.  ybar (nullable) is [n_lambda][M]. */
 int orc_pvalue_sweep(const double *lambda, uint32_t n_lambda, uint32_t n_obs,
-                     uint64_t m_sets, double ybar_obs, uint64_t seed,
+                     uint64_t m_sets, uint64_t base, double ybar_obs, uint64_t seed,
                      uint64_t *counts, double *p, double *ybar, int n_threads);
 
 #ifdef __cplusplus

@@ -93,7 +93,7 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
             "abc_prior_predictive": ([M, P, u64, u64, u64, u32, P, P, P, P], i32),
             "abc_select_workspace_bytes": ([u64], sz),
             "abc_select": ([P, u64, u64, dbl, M, u64, u64, u32, P, P, P, u64, P, P, P, P, sz, P], i32),
-            "pvalue_sweep": ([P, u32, u32, u64, dbl, u64, P, P, P, P], i32),
+            "pvalue_sweep": ([P, u32, u32, u64, u64, dbl, u64, P, P, P, P], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -216,7 +216,8 @@ def abc_select(dist: torch.Tensor, k: int = 0, eps: float = math.inf, model: dic
 
 
 def pvalue_sweep(lambdas: torch.Tensor, n_obs: int, m_sets: int, ybar_obs: float, seed: int,
-                 want_ybar: bool = False, out: dict | None = None, stream=None) -> dict:
+                 want_ybar: bool = False, set_base: int = 0, out: dict | None = None,
+                 stream=None) -> dict:
     """lambdas: [K] f64 (CUDA).  Returns counts [K] u64, p [K] f64, ybar [K,M] f64 | None."""
     K = lambdas.shape[0]
     dev = lambdas.device
@@ -230,7 +231,7 @@ def pvalue_sweep(lambdas: torch.Tensor, n_obs: int, m_sets: int, ybar_obs: float
     ybar = out.get("ybar")
     if want_ybar and ybar is None:
         ybar = torch.empty((K, m_sets), dtype=torch.float64, device=dev)
-    _check(load_library().pvalue_sweep(_ptr(lambdas), K, n_obs, m_sets, float(ybar_obs), seed,
+    _check(load_library().pvalue_sweep(_ptr(lambdas), K, n_obs, m_sets, set_base, float(ybar_obs), seed,
                                        _ptr(counts), _ptr(p), _ptr(ybar if want_ybar else None),
                                        _stream(stream)))
     return {"counts": counts, "p": p, "ybar": ybar if want_ybar else None}

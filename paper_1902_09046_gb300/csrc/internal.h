@@ -38,7 +38,8 @@ cudaError_t launch_select(const double* dist, uint32_t n, uint64_t k, double eps
 
 // p-value sweep.
 cudaError_t launch_pvalue(const double* lambda, uint32_t n_lambda, uint32_t n_obs,
-                          uint32_t m_sets, double ybar_obs, uint64_t seed, uint64_t* counts,
+                          uint32_t m_sets, uint32_t set_base, double ybar_obs, uint64_t seed,
+                          uint64_t* counts,
                           double* p_out, double* ybar_out, cudaStream_t s);
 
 }  // namespace ppabc

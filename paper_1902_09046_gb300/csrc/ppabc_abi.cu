@@ -191,20 +191,23 @@ int abc_select(const double* dist, uint64_t n, uint64_t k, double eps, const ppa
 }
 
 int pvalue_sweep(const double* lambda, uint32_t n_lambda, uint32_t n_obs, uint64_t m_sets,
-                 double ybar_obs, uint64_t seed, uint64_t* counts, double* p_out, double* ybar_out,
-                 void* stream) {
+                 uint64_t set_base, double ybar_obs, uint64_t seed, uint64_t* counts, double* p_out,
+                 double* ybar_out, void* stream) {
   if (n_lambda == 0) return PPABC_OK;
   if (n_lambda > 65535u) return set_error(PPABC_EINVAL, "n_lambda must be <= 65535");
   if (!lambda || !counts) return set_error(PPABC_EINVAL, "lambda and counts must be non-NULL");
   if (n_obs < 1) return set_error(PPABC_EINVAL, "n_obs must be >= 1");
   if (m_sets < 1 || m_sets > 0xFFFFFFFFull) return set_error(PPABC_EINVAL, "m_sets must be in [1, 2^32)");
+  if (set_base > 0x100000000ull - m_sets)
+    return set_error(PPABC_EINVAL, "set_base + m_sets must be <= 2^32");
   if (((static_cast<uint64_t>(n_obs) + 1 + 3) >> 2) > 0xFFFFFFFFull)
     return set_error(PPABC_EINVAL, "n_obs too large");
   if (!isfinite(ybar_obs)) return set_error(PPABC_EINVAL, "ybar_obs must be finite");
   int rc = require_device();
   if (rc) return rc;
-  return check_cuda(launch_pvalue(lambda, n_lambda, n_obs, static_cast<uint32_t>(m_sets), ybar_obs, seed,
-                                  counts, p_out, ybar_out, static_cast<cudaStream_t>(stream)),
+  return check_cuda(launch_pvalue(lambda, n_lambda, n_obs, static_cast<uint32_t>(m_sets),
+                                  static_cast<uint32_t>(set_base), ybar_obs, seed, counts, p_out,
+                                  ybar_out, static_cast<cudaStream_t>(stream)),
                     "pvalue_sweep launch");
 }
 

@@ -28,7 +28,8 @@ __device__ __forceinline__ void kahan_add(float& s, float& comp, float x) {
 template <bool kWantYbar>
 __global__ void __launch_bounds__(kPvThreads) pvalue_tail(const double* __restrict__ lambda,
                                                           uint32_t n_obs, double inv_n,
-                                                          uint32_t m_sets, double abs_ybar_obs,
+                                                          uint32_t m_sets, uint32_t set_base,
+                                                          double abs_ybar_obs,
                                                           uint32_t k0, uint32_t k1,
                                                           unsigned long long* __restrict__ counts,
                                                           double* __restrict__ ybar_out) {
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(kPvThreads) pvalue_tail(const double* __restri
     if (m < m_sets) {
       float z0 = 0.0f, s = 0.0f, comp = 0.0f;
       for (uint32_t b = 0; b < n_full; ++b) {
-        const float4 z = block_normals(b, static_cast<uint32_t>(m), k, kTagPath, k0, k1);
+        const float4 z = block_normals(b, set_base + static_cast<uint32_t>(m), k, kTagPath, k0, k1);
         if (b == 0) {
           z0 = z.x;
         } else {
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(kPvThreads) pvalue_tail(const double* __restri
         kahan_add(s, comp, z.w);
       }
       if (rem) {
-        const float4 z = block_normals(n_full, static_cast<uint32_t>(m), k, kTagPath, k0, k1);
+        const float4 z = block_normals(n_full, set_base + static_cast<uint32_t>(m), k, kTagPath, k0, k1);
         if (n_full == 0) {
           z0 = z.x;
         } else {
@@ -83,8 +84,8 @@ __global__ void pvalue_finalize(const unsigned long long* counts, uint32_t n_lam
 }  // namespace
 
 cudaError_t launch_pvalue(const double* lambda, uint32_t n_lambda, uint32_t n_obs,
-                          uint32_t m_sets, double ybar_obs, uint64_t seed, uint64_t* counts,
-                          double* p_out, double* ybar_out, cudaStream_t s) {
+                          uint32_t m_sets, uint32_t set_base, double ybar_obs, uint64_t seed,
+                          uint64_t* counts, double* p_out, double* ybar_out, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint64_t) * n_lambda, s);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
@@ -103,9 +104,11 @@ cudaError_t launch_pvalue(const double* lambda, uint32_t n_lambda, uint32_t n_ob
   const double a = fabs(ybar_obs);
   auto* c = reinterpret_cast<unsigned long long*>(counts);
   if (ybar_out)
-    pvalue_tail<true><<<grid, kPvThreads, 0, s>>>(lambda, n_obs, inv_n, m_sets, a, k0, k1, c, ybar_out);
+    pvalue_tail<true><<<grid, kPvThreads, 0, s>>>(lambda, n_obs, inv_n, m_sets, set_base, a, k0, k1, c,
+                                                   ybar_out);
   else
-    pvalue_tail<false><<<grid, kPvThreads, 0, s>>>(lambda, n_obs, inv_n, m_sets, a, k0, k1, c, ybar_out);
+    pvalue_tail<false><<<grid, kPvThreads, 0, s>>>(lambda, n_obs, inv_n, m_sets, set_base, a, k0, k1, c,
+                                                    ybar_out);
   e = cudaGetLastError();
   if (e != cudaSuccess || !p_out) return e;
   pvalue_finalize<<<(n_lambda + 127) / 128, 128, 0, s>>>(c, n_lambda, static_cast<double>(m_sets), p_out);

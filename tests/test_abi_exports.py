@@ -80,7 +80,11 @@ def test_invalid_arguments_fail_before_any_launch(lib):
                       0, ctypes.c_void_p(16), None, None, ctypes.c_void_p(256), 8, None)
     assert rc == binding.PPABC_ENOMEM
     # p-value sweep: zero data sets
-    rc = b.pvalue_sweep(ctypes.c_void_p(16), 4, 50, 0, 1.0, 2, ctypes.c_void_p(16), None, None, None)
+    rc = b.pvalue_sweep(ctypes.c_void_p(16), 4, 50, 0, 0, 1.0, 2, ctypes.c_void_p(16), None, None, None)
+    assert rc == binding.PPABC_EINVAL
+    # p-value sweep: data-set range past 2^32
+    rc = b.pvalue_sweep(ctypes.c_void_p(16), 4, 50, 10, (1 << 32) - 5, 1.0, 2, ctypes.c_void_p(16),
+                        None, None, None)
     assert rc == binding.PPABC_EINVAL
 
 
