@@ -168,6 +168,34 @@ int abc_select(const double *dist, uint64_t n, uint64_t k, double eps,
                uint64_t *n_acc_out, double *eps_out, double *post_out,
                void *workspace, size_t workspace_bytes, void *stream);
 
+/* Largest n that abc_select_static accepts. */
+#define PPABC_STATIC_SELECT_MAX_N (1ull << 24)
+
+/*
+ * abc_select without a workspace argument: identical arguments, outputs and
+ * results, but the scratch memory is a fixed static device array inside the
+ * library (about 330 KB, held on every GPU that loads the library until the
+ * process exits), so the call allocates no memory of any kind.  The paper
+ * has no counterpart; this entry point exists for callers that cannot
+ * provide device memory -- for example a service that forbids allocation
+ * once it is running (an allocation can stall the whole device), or a
+ * plug-in hosted by a framework whose allocator it cannot reach.
+ *   - n must be <= PPABC_STATIC_SELECT_MAX_N; larger n gives PPABC_EINVAL.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before
+ *     any stream capture.
+ *   - Every call uses the same array and clears what must start at zero, so
+ *     calls whose work overlaps on the GPU (different streams, or different
+ *     host threads without ordering) race with each other; order them on one
+ *     stream.
+ */
+int abc_select_static(const double *dist, uint64_t n, uint64_t k, double eps,
+                      const ppabc_ou_model *h_model, uint64_t sample_base,
+                      uint64_t seed, uint32_t substream, const float *theta,
+                      uint32_t *idx_out, float *rec_out, uint64_t cap,
+                      uint64_t *n_acc_out, double *eps_out, double *post_out,
+                      void *stream);
+
 /*
  * Prior-predictive p-value sweep (Sec. 4.1, Eq. 6 and Eq. 8) for the
  * conjugate model y_i ~ N(mu, 1), i = 1..n_obs, mu ~ N(0, lambda_k^2).  For

@@ -34,7 +34,8 @@ _ERRNAMES = {PPABC_EINVAL: "EINVAL", PPABC_ENOMEM: "ENOMEM", PPABC_ECUDA: "ECUDA
 # Every symbol include/ppabc.h declares (checked by the CPU test-suite).
 EXPORTED = ("ppabc_abi_version", "ppabc_last_error", "ppabc_device_check", "ppabc_philox_raw",
             "ppabc_normals", "abc_prior_predictive", "abc_select_workspace_bytes", "abc_select",
-            "pvalue_sweep")
+            "abc_select_static", "pvalue_sweep")
+STATIC_SELECT_MAX_N = 1 << 24
 
 
 class PPABCError(RuntimeError):
@@ -93,6 +94,7 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
             "abc_prior_predictive": ([M, P, u64, u64, u64, u32, P, P, P, P], i32),
             "abc_select_workspace_bytes": ([u64], sz),
             "abc_select": ([P, u64, u64, dbl, M, u64, u64, u32, P, P, P, u64, P, P, P, P, sz, P], i32),
+            "abc_select_static": ([P, u64, u64, dbl, M, u64, u64, u32, P, P, P, u64, P, P, P, P], i32),
             "pvalue_sweep": ([P, u32, u32, u64, u64, dbl, u64, P, P, P, P], i32),
         }
         for name, (args, res) in sig.items():
@@ -213,6 +215,37 @@ def abc_select(dist: torch.Tensor, k: int = 0, eps: float = math.inf, model: dic
                           _ptr(post), _ptr(workspace), workspace.numel() * workspace.element_size(),
                           _stream(stream)))
     return {"idx": idx[:cap], "rec": rec[:cap], "n_acc": n_acc, "eps": eps_t, "post": post}
+
+
+def abc_select_static(dist: torch.Tensor, k: int = 0, eps: float = math.inf,
+                      model: dict | None = None, seed: int = 0, substream: int = 0,
+                      sample_base: int = 0, theta: torch.Tensor | None = None,
+                      cap: int | None = None, out: dict | None = None, stream=None) -> dict:
+    """abc_select whose scratch is the library's static device array: for
+    callers that cannot allocate device memory.  At most STATIC_SELECT_MAX_N
+    distances; calls that overlap on the GPU race on the shared scratch.
+    The output tensors are allocated here unless passed in ``out``."""
+    n = dist.shape[0]
+    if cap is None:
+        cap = k if k > 0 else n
+    dev = dist.device
+    out = dict(out or {})
+    res = {"idx": out.get("idx"), "rec": out.get("rec"), "n_acc": out.get("n_acc"),
+           "eps": out.get("eps"), "post": out.get("post")}
+    shapes = {"idx": ((max(cap, 1),), torch.uint32), "rec": ((max(cap, 1), 4), torch.float32),
+              "n_acc": ((1,), torch.uint64), "eps": ((1,), torch.float64),
+              "post": ((6,), torch.float64)}
+    for key, (shape, dtype) in shapes.items():
+        if res[key] is None:
+            res[key] = torch.empty(shape, dtype=dtype, device=dev)
+    mdl = ctypes.byref(OUModel.from_dict(model)) if model is not None else None
+    _check(load_library().abc_select_static(
+        _ptr(dist), n, k, float(eps), mdl, sample_base, seed, substream, _ptr(theta),
+        _ptr(res["idx"]), _ptr(res["rec"]), cap, _ptr(res["n_acc"]), _ptr(res["eps"]),
+        _ptr(res["post"]), _stream(stream)))
+    res["idx"] = res["idx"][:cap]
+    res["rec"] = res["rec"][:cap]
+    return res
 
 
 def pvalue_sweep(lambdas: torch.Tensor, n_obs: int, m_sets: int, ybar_obs: float, seed: int,
