@@ -50,6 +50,13 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--mode", choices=("path", "batch", "serve"), default="path",
+                    help="path: the headline step; batch: 256 uneven jobs, plain vs persistent; "
+                         "serve: Poisson arrivals, served vs plain")
+    ap.add_argument("--jobs", type=int, default=256)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--abc-samples", type=int, default=1 << 24)
     ap.add_argument("--abc-steps", type=int, default=10_000)
     ap.add_argument("--pv-sets", type=int, default=1_000_000)
@@ -381,10 +388,163 @@ def gpu_arm(args):
     return 0
 
 
+def job_specs(jobs):
+    return [{"model": j.model, "y_obs": j.y_obs, "n_samples": j.n, "seed": j.seed, "k": j.k_accept}
+            for j in jobs]
+
+
+def batch_mode(args):
+    """256 uneven OU-ABC jobs: one job per launch pair (plain) against one
+    persistent, graph-replayed launch (batched); same results either way."""
+    import torch
+    from paper_1902_09046_gb300 import autotune, binding
+    from paper_1902_09046_gb300 import build as libbuild
+
+    torch.cuda.set_device(0)
+    libbuild.build()
+    binding.device_check()
+    jobs = workloads.batched_jobs(args.jobs)
+    specs = job_specs(jobs)
+    total_steps = sum(j.path_steps for j in jobs)
+    dev = torch.device("cuda")
+    stream = torch.cuda.Stream()
+    max_n = max(j.n for j in jobs)
+    dist = torch.empty(max_n, dtype=torch.float64, device=dev)
+    ws = torch.empty(binding.abc_select_workspace_bytes(max_n), dtype=torch.uint8, device=dev)
+    outs = [{"idx": torch.empty(j.k_accept, dtype=torch.uint32, device=dev),
+             "rec": torch.empty((j.k_accept, 4), dtype=torch.float32, device=dev),
+             "n_acc": torch.empty(1, dtype=torch.uint64, device=dev),
+             "eps": torch.empty(1, dtype=torch.float64, device=dev),
+             "post": torch.empty(6, dtype=torch.float64, device=dev)} for j in jobs]
+
+    def plain():
+        for j, o in zip(jobs, outs):
+            binding.abc_prior_predictive(j.model, j.y_obs, j.n, j.seed, want_theta=False,
+                                         out={"dist": dist[:j.n]}, stream=stream)
+            binding.abc_select(dist[:j.n], k=j.k_accept, model=j.model, seed=j.seed,
+                               workspace=ws, out=o, stream=stream)
+
+    def timed(fn, reps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        stream.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    with torch.cuda.stream(stream):
+        t_tune = time.perf_counter()
+        tile = autotune.tune(specs)
+        t_tune = time.perf_counter() - t_tune
+        batch = binding.Batch(specs, tile=tile, stream=stream)
+        plain()
+        batch.launch(graph=True, stream=stream)
+        stream.synchronize()
+        with ClockSampler(0) as clocks:
+            ms_plain = timed(plain, args.steps)
+            ms_batch = timed(lambda: batch.launch(graph=True, stream=stream), args.steps)
+        # the two forms give identical accepted sets
+        same = True
+        for o, r in zip(outs, batch.results()):
+            same &= bool(torch.equal(o["idx"], r["idx"])) and bool(torch.equal(o["post"], r["post"]))
+        batch.close()
+    plain_ms = statistics.median(ms_plain)
+    batch_ms = statistics.median(ms_batch)
+    line = {"mode": "batch", "metric": "EM path-steps/sec, batched vs plain", "unit": UNIT,
+            "value": total_steps / (batch_ms / 1e3), "plain_value": total_steps / (plain_ms / 1e3),
+            "speedup": plain_ms / batch_ms, "batch_ms": batch_ms, "plain_ms": plain_ms,
+            "path_steps": total_steps, "jobs": len(jobs), "tile": list(tile),
+            "autotune_s": t_tune, "results_identical": same, "steps": args.steps,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": f"{len(jobs)} OU-ABC jobs, N log-uniform [1e3,1e7], "
+                                   f"S uniform {{100..10^4}}, dt=10/S, 1% accepted"},
+            "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def serve_mode(args):
+    """Poisson arrivals of mixed ABC / p-value jobs replayed in real time
+    against the server with `--slots` streams (served) and with one stream
+    (plain, one job at a time); p50/p99 latency and aggregate throughput."""
+    import threading as th
+
+    import torch
+    from paper_1902_09046_gb300 import binding
+    from paper_1902_09046_gb300 import build as libbuild
+
+    torch.cuda.set_device(0)
+    libbuild.build()
+    binding.device_check()
+    jobs = workloads.served_jobs(rate_per_s=args.serve_rate, duration_s=args.serve_seconds)
+    reqs = [binding.abc_request(j.model, j.y_obs, j.n, j.k_accept, j.seed) if j.kind == "abc"
+            else binding.pvalue_request(j.lam, j.n_obs, j.n, j.ybar_obs, j.seed) for j in jobs]
+    total_steps = sum(j.path_steps for j in jobs)
+    arena = 64 << 30
+
+    def run(slots):
+        with binding.Server(arena, n_slots=slots) as srv:
+            # warm-up: a few jobs of each kind
+            for r in reqs[:8]:
+                srv.release(srv.wait(srv.submit(r), 120.0)["job_id"])
+            ids = [None] * len(jobs)
+            t0 = time.perf_counter()
+
+            def client():
+                for i, (j, r) in enumerate(zip(jobs, reqs)):
+                    delay = j.arrival_s - (time.perf_counter() - t0)
+                    if delay > 0:
+                        time.sleep(delay)
+                    ids[i] = srv.submit(r)
+
+            c = th.Thread(target=client)
+            c.start()
+            c.join()
+            res = [srv.wait(i, 600.0) for i in ids]
+            t_end = time.perf_counter()
+            lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+            first = min(r["t_submit"] for r in res)
+            last = max(r["t_done"] for r in res)
+            st = srv.stats()
+            for i in ids:
+                srv.release(i)
+        ok = all(r["status"] == binding.PPABC_OK for r in res)
+        kinds = np.array([j.kind == "abc" for j in jobs])
+        return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "p99_abc_ms": float(np.percentile(lat[kinds], 99) * 1e3),
+                "p99_pvalue_ms": float(np.percentile(lat[~kinds], 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
+                "throughput": total_steps / (last - first), "makespan_s": last - first,
+                "wall_s": t_end - t0, "all_ok": ok, "peak_arena_bytes": st["peak_arena_bytes"],
+                "results": [(r["n_acc"], r["eps"], r["count"]) for r in res]}
+
+    with ClockSampler(0) as clocks:
+        served = run(args.slots)
+        plain = run(1)
+    same = served.pop("results") == plain.pop("results")
+    line = {"mode": "serve", "metric": "p50/p99 job latency and aggregate path-steps/s, served vs plain",
+            "unit": "ms", "value": served["p99_ms"], "higher_is_better": False,
+            "served": served, "plain": plain, "slots": args.slots, "jobs": len(jobs),
+            "path_steps": total_steps, "results_identical": same,
+            "offered_path_steps_per_s": total_steps / args.serve_seconds,
+            "config": {"workload": f"Poisson {args.serve_rate:g}/s for {args.serve_seconds:g} s, 70% OU-ABC "
+                                   f"(N log-U[1e3,1e6], S U{{100..2000}}), 30% p-value (n=50, M log-U[1e4,1e6], "
+                                   f"lambda log-U[0.01,100]), HBM arena 64 GiB"},
+            "data": "synthetic (seeded)", "dtype": "f32", "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.mode == "batch":
+        return batch_mode(args)
+    if args.mode == "serve":
+        return serve_mode(args)
     return gpu_arm(args)
 
 

@@ -60,6 +60,7 @@ extern "C" {
 #define PPABC_ETIMEOUT (-4)   /* a bounded device-side wait expired */
 #define PPABC_ENODEV (-5)     /* no sm_103 device current */
 #define PPABC_ECANCELLED (-6) /* job cancelled by the host */
+#define PPABC_PENDING 1       /* server job not finished yet (not an error) */
 
 /* Most observations a model may have. */
 #define PPABC_MAX_OBS 32
@@ -67,6 +68,7 @@ extern "C" {
 /* Counter tags. */
 #define PPABC_TAG_PRIOR 0u
 #define PPABC_TAG_PATH 1u
+#define PPABC_TAG_BASE 2u /* base-prior data sets of the weak-informativity test */
 
 /*
  * Ornstein-Uhlenbeck model of the ABC workloads:
@@ -112,6 +114,15 @@ int ppabc_philox_raw(uint64_t seed, const uint32_t *ctr, uint64_t n,
  */
 int ppabc_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag,
                   uint64_t j0, uint64_t n, float *z, void *stream);
+
+/*
+ * Box-Muller transform of given word pairs, in binary32: w is [n][2] uint32
+ * (even, odd), z is [n][2] float with z_even = r cos 2 pi u(w_odd),
+ * z_odd = r sin 2 pi u(w_odd), r = sqrt(-2 ln u(w_even)).  Exposes the
+ * transform every normal of the library goes through, so it can be checked
+ * on all 2^23 uniforms.  w and z 8-byte aligned.
+ */
+int ppabc_box_muller(const uint32_t *w, uint64_t n, float *z, void *stream);
 
 /*
  * Prior-predictive sampling for ABC (Sec. 3.1, Eq. 2; Algorithm 1 with N
@@ -197,6 +208,158 @@ int abc_select_static(const double *dist, uint64_t n, uint64_t k, double eps,
                       void *stream);
 
 /*
+ * ---------------------------------------------------------------------------
+ * Batched execution: many uneven OU-ABC jobs in one persistent launch.
+ * ---------------------------------------------------------------------------
+ * One job is abc_prior_predictive over samples 0..n_samples-1 followed by
+ * abc_select with theta redrawn from the prior counter; results are
+ * bit-identical to running the job alone with those two calls.
+ */
+typedef struct ppabc_abc_job {
+  ppabc_ou_model model;
+  double y_obs[PPABC_MAX_OBS]; /* observed summaries (first model.n_obs used) */
+  uint64_t n_samples;          /* 1 .. 2^32-1 */
+  uint64_t seed;
+  uint32_t substream;
+  uint32_t reserved;
+  uint64_t k;                  /* > 0: k nearest; 0: dist <= eps */
+  double eps;
+  double *dist;                /* nullable device [n_samples]: NULL keeps the
+                                  distances in the batch workspace */
+  uint32_t *idx_out;           /* device [cap] */
+  float *rec_out;              /* device [cap][4], 16-byte aligned */
+  uint64_t cap;
+  uint64_t *n_acc_out;         /* device [1] */
+  double *eps_out;             /* nullable device [1] */
+  double *post_out;            /* nullable device [6] */
+} ppabc_abc_job;
+
+/*
+ * Tile shape of the persistent kernel: `threads` per CTA (128 or 256) and the
+ * least number of Euler-Maruyama steps one thread runs per tile (a job with S
+ * steps gets ceil(min_tile_steps / S) samples per thread, capped at 64).
+ * NULL selects (128, 4096).  The Python binding's autotuner picks it.
+ */
+typedef struct ppabc_tile_config {
+  uint32_t threads;
+  uint32_t min_tile_steps;
+} ppabc_tile_config;
+
+/* Opaque host-side plan of a prepared batch. */
+typedef struct ppabc_batch_plan ppabc_batch_plan;
+
+/* Workspace bytes for a batch (job table, schedule, distances of jobs with
+ * dist == NULL, selection scratch). */
+size_t ppabc_batch_workspace_bytes(const ppabc_abc_job *h_jobs, uint32_t n_jobs);
+
+/*
+ * Validates the jobs, uploads the job table into `workspace` and synchronises
+ * `stream` once (the upload is the only host-device transfer of a batch).
+ * The plan refers to the workspace and to the jobs' output pointers, which
+ * must stay valid while the plan is used.
+ */
+int ppabc_batch_prepare(const ppabc_abc_job *h_jobs, uint32_t n_jobs,
+                        const ppabc_tile_config *h_cfg, void *workspace,
+                        size_t workspace_bytes, void *stream,
+                        ppabc_batch_plan **plan_out);
+
+/* Enqueues the batch (persistent simulation kernel, then one selection per
+ * job) on `stream`; no host synchronisation. */
+int ppabc_batch_launch(ppabc_batch_plan *plan, void *stream);
+
+/* As ppabc_batch_launch, but the first call captures the launch into a CUDA
+ * graph kept in the plan and every call replays it.  `stream` must not be the
+ * legacy default stream. */
+int ppabc_batch_launch_graph(ppabc_batch_plan *plan, void *stream);
+
+/* Releases the plan (and its graph).  NULL is allowed. */
+int ppabc_batch_plan_destroy(ppabc_batch_plan *plan);
+
+/* prepare + launch + destroy. */
+int ppabc_batch_run(const ppabc_abc_job *h_jobs, uint32_t n_jobs,
+                    const ppabc_tile_config *h_cfg, void *workspace,
+                    size_t workspace_bytes, void *stream);
+
+/*
+ * ---------------------------------------------------------------------------
+ * Request server: continuous batching of ABC and p-value jobs.
+ * ---------------------------------------------------------------------------
+ * Jobs may be submitted from any host thread at any time.  A scheduler thread
+ * admits them in arrival order as soon as one of `n_slots` CUDA streams is
+ * free and the job's device footprint fits in the caller's arena (the HBM
+ * admission cap), then enqueues the job's whole pipeline on that stream;
+ * jobs on different streams overlap on the GPU.  n_slots = 1 gives the plain
+ * one-job-at-a-time form.  The server allocates no device memory: every job
+ * buffer is carved from the arena.  Accepted samples of an ABC job stay in
+ * the arena until ppabc_server_release.  Timestamps are seconds on the
+ * server's monotonic clock (ppabc_server_now).
+ *
+ * An ABC job is abc_prior_predictive over samples 0..n_samples-1 (seed,
+ * substream) followed by abc_select of the k nearest with theta redrawn; a
+ * p-value job is pvalue_sweep with one lambda.  Results are bit-identical to
+ * the same job run alone through those calls.
+ */
+#define PPABC_JOB_ABC 0
+#define PPABC_JOB_PVALUE 1
+
+typedef struct ppabc_request {
+  int32_t kind;                /* PPABC_JOB_ABC or PPABC_JOB_PVALUE */
+  uint32_t substream;          /* ABC only */
+  uint64_t seed;
+  ppabc_ou_model model;        /* ABC */
+  double y_obs[PPABC_MAX_OBS]; /* ABC */
+  uint64_t n_samples;          /* ABC: 1 .. 2^32-1 */
+  uint64_t k;                  /* ABC: accept the k nearest, 1 .. n_samples */
+  double lambda;               /* p-value: prior sd of mu */
+  uint32_t n_obs;              /* p-value: n */
+  uint32_t reserved;
+  uint64_t m_sets;             /* p-value: data sets M */
+  double ybar_obs;             /* p-value */
+} ppabc_request;
+
+typedef struct ppabc_result {
+  int32_t status;              /* PPABC_OK, PPABC_ECANCELLED or PPABC_ECUDA */
+  int32_t kind;
+  uint64_t job_id;
+  double t_submit, t_admit, t_done;
+  uint64_t n_acc;              /* ABC */
+  double eps;                  /* ABC */
+  double post[6];              /* ABC: posterior means then variances */
+  uint64_t count;              /* p-value: tail count */
+  double p;                    /* p-value */
+} ppabc_result;
+
+typedef struct ppabc_server_stats {
+  uint64_t submitted, admitted, completed, failed, cancelled, queued, running;
+  uint64_t arena_used_bytes, peak_arena_bytes;
+} ppabc_server_stats;
+
+typedef struct ppabc_server ppabc_server;
+
+/* d_arena: device memory the server may use, 256-byte aligned, >= 4096 bytes. */
+int ppabc_server_create(void *d_arena, size_t arena_bytes, uint32_t n_slots,
+                        ppabc_server **out);
+/* PPABC_ENOMEM if the job could never fit in the arena. */
+int ppabc_server_submit(ppabc_server *s, const ppabc_request *req, uint64_t *job_id);
+/* PPABC_OK and *out filled when finished, PPABC_PENDING otherwise. */
+int ppabc_server_poll(ppabc_server *s, uint64_t job_id, ppabc_result *out);
+/* Waits up to timeout_s seconds; PPABC_ETIMEOUT if still running. */
+int ppabc_server_wait(ppabc_server *s, uint64_t job_id, double timeout_s,
+                      ppabc_result *out);
+/* Copies up to cap accepted (index, record) pairs of a finished ABC job to
+ * host memory (h_idx [cap] uint32, h_rec [cap][4] float; either nullable). */
+int ppabc_server_fetch(ppabc_server *s, uint64_t job_id, uint32_t *h_idx,
+                       float *h_rec, uint64_t cap, uint64_t *n_out);
+/* Frees a finished job's device results and forgets the job. */
+int ppabc_server_release(ppabc_server *s, uint64_t job_id);
+/* A queued job never runs; a running job's result is discarded. */
+int ppabc_server_cancel(ppabc_server *s, uint64_t job_id);
+int ppabc_server_get_stats(ppabc_server *s, ppabc_server_stats *out);
+double ppabc_server_now(ppabc_server *s);
+/* Stops the scheduler after the running jobs finish; NULL is allowed. */
+int ppabc_server_destroy(ppabc_server *s);
+
+/*
  * Prior-predictive p-value sweep (Sec. 4.1, Eq. 6 and Eq. 8) for the
  * conjugate model y_i ~ N(mu, 1), i = 1..n_obs, mu ~ N(0, lambda_k^2).  For
  * lambda index k < n_lambda and data set m = set_base .. set_base+m_sets-1,
@@ -221,6 +384,29 @@ int pvalue_sweep(const double *lambda, uint32_t n_lambda, uint32_t n_obs,
                  uint64_t m_sets, uint64_t set_base, double ybar_obs, uint64_t seed,
                  uint64_t *counts, double *p_out, double *ybar_out,
                  void *stream);
+
+/* Most data sets per hyperparameter in weakinf_test. */
+#define PPABC_WEAKINF_MAX_SETS 16384
+
+/*
+ * Weak-informativity test (Sec. 4.1, Eq. 9 and Algorithm 2) for the
+ * conjugate model y_i ~ N(mu, 1), i = 1..n_obs, mu ~ N(0, lambda^2), base
+ * hyperparameter lambda0.  For each k < n_lambda:
+ *   base sets   i < N: ybar_0^i of stream (seed, i, k, BASE) with lambda0,
+ *   lambda sets j < N: ybar_k^j of stream (seed, j, k, PATH) with lambda[k],
+ *   count_k^i = #{j : |ybar_k^j| >= |ybar_0^i|}      (p_k^i = count_k^i / N),
+ *   gamma_out[k] = the ceil(alpha N)-th smallest p_k^i (the alpha quantile).
+ * Priors with gamma_k > gamma_0 for lambda_0 = lambda0 are weakly informative
+ * relative to the base prior (Eq. 9).  ybar as in pvalue_sweep; the
+ * comparisons are binary64.
+ *   lambda      [n_lambda] double (device).
+ *   gamma_out   [n_lambda] double (device).
+ *   counts_out  nullable [n_lambda][N] uint32 (device).
+ * Requires 1 <= N <= PPABC_WEAKINF_MAX_SETS, 0 < alpha <= 1, n_obs >= 1.
+ */
+int weakinf_test(const double *lambda, uint32_t n_lambda, double lambda0,
+                 uint32_t n_obs, uint64_t n_sets, double alpha, uint64_t seed,
+                 double *gamma_out, uint32_t *counts_out, void *stream);
 
 #ifdef __cplusplus
 }

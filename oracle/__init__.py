@@ -27,6 +27,9 @@ _lib = None
 
 TAG_PRIOR = 0
 TAG_PATH = 1
+TAG_BASE = 2
+TAG_TOGGLE_PRIOR = 4
+TAG_TOGGLE_PATH = 5
 
 
 def build(force: bool = False) -> str:
@@ -42,6 +45,11 @@ def build(force: bool = False) -> str:
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+class _ToggleModel(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 7), ("hi", ctypes.c_double * 7),
+                ("T", ctypes.c_uint32), ("C", ctypes.c_uint32)]
 
 
 class _OUModel(ctypes.Structure):
@@ -61,6 +69,8 @@ def _load():
             lib.orc_philox_batch.restype = None
             lib.orc_u01.argtypes = [u32]
             lib.orc_u01.restype = dbl
+            lib.orc_box_muller_words.argtypes = [P, u64, P]
+            lib.orc_box_muller_words.restype = None
             lib.orc_stream_normals.argtypes = [u64, u32, u32, u32, u64, u64, P]
             lib.orc_stream_normals.restype = None
             lib.orc_ou_prior_predictive.argtypes = [ctypes.POINTER(_OUModel), P, u64, u64,
@@ -74,6 +84,11 @@ def _load():
             lib.orc_moments.restype = None
             lib.orc_pvalue_sweep.argtypes = [P, u32, u32, u64, u64, dbl, u64, P, P, P, i32]
             lib.orc_pvalue_sweep.restype = i32
+            lib.orc_weakinf.argtypes = [P, u32, dbl, u32, u64, dbl, u64, P, P, i32]
+            lib.orc_weakinf.restype = i32
+            lib.orc_toggle_prior_predictive.argtypes = [ctypes.POINTER(_ToggleModel), P, u64, u64,
+                                                        u64, u32, P, P, P, P, P, i32]
+            lib.orc_toggle_prior_predictive.restype = i32
             _lib = lib
     return _lib
 
@@ -96,6 +111,14 @@ def philox(seed: int, ctr: np.ndarray) -> np.ndarray:
 
 def u01(w: int) -> float:
     return _load().orc_u01(int(w) & 0xFFFFFFFF)
+
+
+def box_muller_words(w: np.ndarray) -> np.ndarray:
+    """Box-Muller normals of word pairs w [n,2] uint32 -> [n,2] float64."""
+    w = np.ascontiguousarray(w, dtype=np.uint32).reshape(-1, 2)
+    z = np.zeros(w.shape, dtype=np.float64)
+    _load().orc_box_muller_words(_ptr(w), w.shape[0], _ptr(z))
+    return z
 
 
 def stream_normals(seed: int, c1: int, c2: int, tag: int, j0: int, n: int) -> np.ndarray:
@@ -171,3 +194,43 @@ def pvalue_sweep(lambdas, n_obs: int, m_sets: int, ybar_obs: float, seed: int,
     if rc != 0:
         raise ValueError("oracle rejected the p-value arguments")
     return counts, p, ybar
+
+
+def weakinf(lambdas, lambda0: float, n_obs: int, n_sets: int, alpha: float, seed: int,
+            want_counts: bool = False, n_threads: int | None = None):
+    """(gamma [K], counts [K,N] | None): Algorithm 2's alpha-level cut-offs."""
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    K = lam.shape[0]
+    gamma = np.zeros(K, dtype=np.float64)
+    counts = np.zeros((K, n_sets), dtype=np.uint64) if want_counts else None
+    rc = _load().orc_weakinf(_ptr(lam), K, float(lambda0), n_obs, n_sets, float(alpha), seed,
+                             _ptr(gamma), _ptr(counts), n_threads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle rejected the weak-informativity arguments")
+    return gamma, counts
+
+
+def toggle_prior_predictive(model: dict, q_obs, n: int, seed: int, sub: int = 0, base: int = 0,
+                            want_theta: bool = True, want_summ: bool = True, want_y: bool = False,
+                            n_threads: int | None = None, want_uv: bool = False):
+    """(theta [n,7], summ [n,19], y [n,C] | None, dist [n]) of the toggle-switch model;
+    with want_uv a fifth item, the final (u, v) of every cell [n,C,2]."""
+    m = _ToggleModel()
+    for j in range(7):
+        m.lo[j] = float(model["lo"][j])
+        m.hi[j] = float(model["hi"][j])
+    m.T, m.C = int(model["T"]), int(model["C"])
+    q = np.ascontiguousarray(q_obs, dtype=np.float64)
+    theta = np.zeros((n, 7)) if want_theta else None
+    summ = np.zeros((n, 19)) if want_summ else None
+    y = np.zeros((n, m.C)) if want_y else None
+    uv = np.zeros((n, m.C, 2)) if want_uv else None
+    dist = np.zeros(n)
+    rc = _load().orc_toggle_prior_predictive(ctypes.byref(m), _ptr(q), base, n, seed, sub,
+                                             _ptr(theta), _ptr(summ), _ptr(y), _ptr(uv),
+                                             _ptr(dist), n_threads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle rejected the toggle-switch arguments")
+    if want_uv:
+        return theta, summ, y, dist, uv
+    return theta, summ, y, dist

@@ -87,6 +87,10 @@ static void box_muller(uint32_t w_even, uint32_t w_odd, double *z_even,
   *z_odd = r * sin(two_pi * u2);
 }
 
+void orc_box_muller_words(const uint32_t *w, uint64_t n, double *z) {
+  for (uint64_t i = 0; i < n; ++i) box_muller(w[2 * i], w[2 * i + 1], &z[2 * i], &z[2 * i + 1]);
+}
+
 /* The four normals of counter block (b, c1, c2, tag). */
 static void block_normals(const uint32_t key[2], uint32_t b, uint32_t c1,
                           uint32_t c2, uint32_t tag, double z[4]) {
@@ -308,6 +312,22 @@ void orc_moments(const double *theta, const uint64_t *idx, uint64_t k,
  * probability is estimated by the indicator count of Algorithm 2's inner
  * loop over M prior-predictive data sets.
  * ------------------------------------------------------------------------- */
+/* ybar of one prior-predictive data set: normals z_0..z_n of stream
+ * (seed, c1, c2, tag), mu = lam z_0, ybar = mu + (1/n) sum_{t=1..n} z_t. */
+static double ybar_of(const uint32_t key[2], double lam, uint32_t n_obs, uint32_t c1, uint32_t c2,
+                      uint32_t tag) {
+  double z[4];
+  double mu = 0.0, s = 0.0;
+  for (uint32_t t = 0; t <= n_obs; ++t) {
+    if (t % 4 == 0) block_normals(key, t / 4, c1, c2, tag, z);
+    if (t == 0)
+      mu = lam * z[0];
+    else
+      s += z[t % 4];
+  }
+  return mu + s / (double)n_obs;
+}
+
 typedef struct pv_job {
   const double *lambda;
   uint32_t n_lambda, n_obs;
@@ -320,24 +340,13 @@ typedef struct pv_job {
 
 static void *pv_worker(void *arg) {
   pv_job *J = (pv_job *)arg;
-  double *z = (double *)malloc(((size_t)J->n_obs + 4) * sizeof(double));
   for (uint64_t f = J->lo; f < J->hi; ++f) {
     uint32_t k = (uint32_t)(f / J->m_sets);
     uint64_t m = J->base + f % J->m_sets;
-    /* normals 0..n of stream (seed, m, k, PATH) */
-    for (uint32_t t = 0; t <= J->n_obs; ++t) {
-      double zb[4];
-      block_normals(J->key, t / 4, (uint32_t)m, k, ORC_TAG_PATH, zb);
-      z[t] = zb[t % 4];
-    }
-    double mu = J->lambda[k] * z[0];
-    double s = 0.0;
-    for (uint32_t t = 1; t <= J->n_obs; ++t) s += z[t];
-    double ybar = mu + s / (double)J->n_obs;
+    double ybar = ybar_of(J->key, J->lambda[k], J->n_obs, (uint32_t)m, k, ORC_TAG_PATH);
     if (J->ybar) J->ybar[f] = ybar;
     if (fabs(ybar) >= fabs(J->ybar_obs)) J->counts[k] += 1;
   }
-  free(z);
   return NULL;
 }
 
@@ -385,4 +394,259 @@ int orc_pvalue_sweep(const double *lambda, uint32_t n_lambda, uint32_t n_obs,
   free(th);
   free(priv);
   return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Weak-informativity test (Sec. 4.1, Eq. 9 and Algorithm 2) for the conjugate
+ * normal model.  Algorithm 2 draws, for every hyperparameter lambda_k, N data
+ * sets from the base prior predictive and N from the lambda_k prior
+ * predictive, estimates the p-value of every base data set under lambda_k by
+ * the indicator average over the lambda_k data sets, and returns the alpha
+ * quantile of those p-values.  With the sufficient statistic ybar, whose
+ * prior predictive density under lambda falls with |ybar|, the event
+ * pi(D_k^j | lambda_k) <= pi(D_0^i | lambda_k) is |ybar_k^j| >= |ybar_0^i|.
+ * The comparisons are done by brute force over all (i, j) pairs.
+ * ------------------------------------------------------------------------- */
+static int cmp_u64_asc(const void *a, const void *b) { return cmp_u64(a, b); }
+
+typedef struct wi_job {
+  const double *lambda;
+  double lambda0;
+  uint32_t n_obs, k_lo, k_hi;
+  uint64_t n_sets;
+  double alpha;
+  uint32_t key[2];
+  double *gamma;
+  uint64_t *counts;
+  int rc;
+} wi_job;
+
+static void *wi_worker(void *arg) {
+  wi_job *J = (wi_job *)arg;
+  const uint64_t N = J->n_sets;
+  double *y0 = (double *)malloc(N * sizeof(double));
+  double *yk = (double *)malloc(N * sizeof(double));
+  uint64_t *cnt = (uint64_t *)malloc(N * sizeof(uint64_t));
+  if (!y0 || !yk || !cnt) {
+    J->rc = -1;
+    free(y0);
+    free(yk);
+    free(cnt);
+    return NULL;
+  }
+  for (uint32_t k = J->k_lo; k < J->k_hi; ++k) {
+    for (uint64_t i = 0; i < N; ++i) {
+      y0[i] = ybar_of(J->key, J->lambda0, J->n_obs, (uint32_t)i, k, ORC_TAG_BASE);
+      yk[i] = ybar_of(J->key, J->lambda[k], J->n_obs, (uint32_t)i, k, ORC_TAG_PATH);
+    }
+    for (uint64_t i = 0; i < N; ++i) {
+      uint64_t c = 0;
+      for (uint64_t j = 0; j < N; ++j)
+        if (fabs(yk[j]) >= fabs(y0[i])) ++c;
+      cnt[i] = c;
+      if (J->counts) J->counts[(uint64_t)k * N + i] = c;
+    }
+    qsort(cnt, (size_t)N, sizeof(uint64_t), cmp_u64_asc);
+    uint64_t r = (uint64_t)ceil(J->alpha * (double)N);
+    if (r < 1) r = 1;
+    if (r > N) r = N;
+    J->gamma[k] = (double)cnt[r - 1] / (double)N;
+  }
+  free(y0);
+  free(yk);
+  free(cnt);
+  return NULL;
+}
+
+int orc_weakinf(const double *lambda, uint32_t n_lambda, double lambda0, uint32_t n_obs,
+                uint64_t n_sets, double alpha, uint64_t seed, double *gamma,
+                uint64_t *counts, int n_threads) {
+  if (!lambda || !gamma || n_lambda == 0 || n_obs == 0 || n_sets == 0) return -1;
+  if (n_sets > 0x100000000ull || !(alpha > 0.0 && alpha <= 1.0)) return -1;
+  if (n_threads < 1) n_threads = 1;
+  if ((uint32_t)n_threads > n_lambda) n_threads = (int)n_lambda;
+  wi_job *jobs = (wi_job *)calloc((size_t)n_threads, sizeof(wi_job));
+  pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+  if (!jobs || !th) {
+    free(jobs);
+    free(th);
+    return -1;
+  }
+  for (int t = 0; t < n_threads; ++t) {
+    wi_job *J = &jobs[t];
+    J->lambda = lambda;
+    J->lambda0 = lambda0;
+    J->n_obs = n_obs;
+    J->k_lo = (uint32_t)((uint64_t)n_lambda * t / n_threads);
+    J->k_hi = (uint32_t)((uint64_t)n_lambda * (t + 1) / n_threads);
+    J->n_sets = n_sets;
+    J->alpha = alpha;
+    seed_to_key(seed, J->key);
+    J->gamma = gamma;
+    J->counts = counts;
+  }
+  for (int t = 1; t < n_threads; ++t) pthread_create(&th[t], NULL, wi_worker, &jobs[t]);
+  wi_worker(&jobs[0]);
+  int rc = jobs[0].rc;
+  for (int t = 1; t < n_threads; ++t) {
+    pthread_join(th[t], NULL);
+    if (jobs[t].rc) rc = jobs[t].rc;
+  }
+  free(jobs);
+  free(th);
+  return rc;
+}
+
+/* ---------------------------------------------------------------------------
+ * Genetic toggle switch prior predictive (Sec. 3.2, Eq. 3-4; Euler-Maruyama
+ * with Delta t = 1 as in Sec. 3.3, Eq. 5; the per-cell update and the noisy
+ * observation as the paper's C implementation orders them, Sec. 3.4).
+ * For each cell: u = v = 10; for j = 1..T-1
+ *     p_u = v^beta_u, p_v = u^beta_v            (previous values)
+ *     u = 0.97 u + alpha_u / (1 + p_u) - 1 + 0.5 zeta_u
+ *     v = 0.97 v + alpha_v / (1 + p_v) - 1 + 0.5 zeta_v
+ *     u = max(u, 1), v = max(v, 1)
+ * then y = max(u + mu + mu sigma eta / u^gamma, 1).  The summaries are the
+ * 19 equally spaced quantiles of the C values (Vo et al.'s choice, cited in
+ * Sec. 3.2); rho is the Euclidean distance to the observed quantiles.
+ * ------------------------------------------------------------------------- */
+static int cmp_double_asc(const void *a, const void *b) {
+  double x = *(const double *)a, y = *(const double *)b;
+  return (x > y) - (x < y);
+}
+
+/* Quantile at level k/20 of sorted x[0..C-1]: h = (C-1) k / 20, linear
+ * interpolation between x[floor(h)] and the next order statistic. */
+static double quantile_k20(const double *x, uint32_t C, uint32_t k) {
+  uint64_t num = (uint64_t)(C - 1) * k;
+  uint64_t lo = num / 20;
+  double frac = (double)(num % 20) / 20.0;
+  if (lo + 1 >= C) return x[C - 1];
+  return x[lo] + frac * (x[lo + 1] - x[lo]);
+}
+
+static void toggle_one_sample(const orc_toggle_model *m, const double *q_obs,
+                              const uint32_t key[2], uint64_t g, uint32_t sub, double *theta,
+                              double *summ, double *ycell, double *uv, double *dist, double *ybuf) {
+  uint32_t w0[4], w1[4];
+  uint32_t c0[4] = {0u, (uint32_t)g, sub, ORC_TAG_TOGGLE_PRIOR};
+  uint32_t c1[4] = {1u, (uint32_t)g, sub, ORC_TAG_TOGGLE_PRIOR};
+  orc_philox4x32_10(c0, key, w0);
+  orc_philox4x32_10(c1, key, w1);
+  const uint32_t words[7] = {w0[0], w0[1], w0[2], w0[3], w1[0], w1[1], w1[2]};
+  double th[7];
+  for (int j = 0; j < 7; ++j) th[j] = m->lo[j] + (m->hi[j] - m->lo[j]) * orc_u01(words[j]);
+  if (theta)
+    for (int j = 0; j < 7; ++j) theta[j] = th[j];
+  const double mu = th[0], sigma = th[1], gam = th[2];
+  const double alpha_u = th[3], alpha_v = th[4], beta_u = th[5], beta_v = th[6];
+  const uint32_t T = m->T, C = m->C;
+  const uint32_t tag = (sub << 8) | ORC_TAG_TOGGLE_PATH;
+  for (uint32_t c = 0; c < C; ++c) {
+    double u = 10.0, v = 10.0;
+    double z[4];
+    uint32_t zi = 0; /* index of the next normal of this cell's stream */
+    for (uint32_t j = 1; j < T; ++j) {
+      double p_u = pow(v, beta_u);
+      double p_v = pow(u, beta_v);
+      double zu, zv;
+      if (zi % 4 == 0) block_normals(key, zi / 4, (uint32_t)g, c, tag, z);
+      zu = z[zi % 4];
+      ++zi;
+      if (zi % 4 == 0) block_normals(key, zi / 4, (uint32_t)g, c, tag, z);
+      zv = z[zi % 4];
+      ++zi;
+      u = 0.97 * u + alpha_u / (1.0 + p_u) - 1.0 + 0.5 * zu;
+      v = 0.97 * v + alpha_v / (1.0 + p_v) - 1.0 + 0.5 * zv;
+      if (u < 1.0) u = 1.0;
+      if (v < 1.0) v = 1.0;
+    }
+    if (uv) {
+      uv[2 * c] = u;
+      uv[2 * c + 1] = v;
+    }
+    if (zi % 4 == 0) block_normals(key, zi / 4, (uint32_t)g, c, tag, z);
+    double eta = z[zi % 4];
+    double yv = u + mu + mu * sigma * eta / pow(u, gam);
+    if (yv < 1.0) yv = 1.0;
+    ybuf[c] = yv;
+    if (ycell) ycell[c] = yv;
+  }
+  qsort(ybuf, C, sizeof(double), cmp_double_asc);
+  double acc = 0.0;
+  for (uint32_t k = 1; k <= ORC_TOGGLE_NQ; ++k) {
+    double q = quantile_k20(ybuf, C, k);
+    if (summ) summ[k - 1] = q;
+    double r = q - q_obs[k - 1];
+    acc += r * r;
+  }
+  *dist = sqrt(acc);
+}
+
+typedef struct tg_job {
+  const orc_toggle_model *m;
+  const double *q_obs;
+  uint32_t key[2];
+  uint64_t base, lo, hi;
+  uint32_t sub;
+  double *theta, *summ, *y, *uv, *dist;
+  int rc;
+} tg_job;
+
+static void *tg_worker(void *arg) {
+  tg_job *J = (tg_job *)arg;
+  double *ybuf = (double *)malloc((size_t)J->m->C * sizeof(double));
+  if (!ybuf) {
+    J->rc = -1;
+    return NULL;
+  }
+  for (uint64_t t = J->lo; t < J->hi; ++t)
+    toggle_one_sample(J->m, J->q_obs, J->key, J->base + t, J->sub,
+                      J->theta ? J->theta + 7 * t : NULL,
+                      J->summ ? J->summ + ORC_TOGGLE_NQ * t : NULL,
+                      J->y ? J->y + (uint64_t)J->m->C * t : NULL,
+                      J->uv ? J->uv + 2 * (uint64_t)J->m->C * t : NULL, J->dist + t, ybuf);
+  free(ybuf);
+  return NULL;
+}
+
+int orc_toggle_prior_predictive(const orc_toggle_model *m, const double *q_obs, uint64_t base,
+                                uint64_t n, uint64_t seed, uint32_t sub, double *theta,
+                                double *summ, double *y, double *uv, double *dist, int n_threads) {
+  if (!m || !q_obs || !dist || m->T < 2 || m->C < 1) return -1;
+  if (sub > 0xFFFFFFu || base + n > 0x100000000ull) return -1;
+  if (n_threads < 1) n_threads = 1;
+  if ((uint64_t)n_threads > n) n_threads = (int)(n > 0 ? n : 1);
+  tg_job *jobs = (tg_job *)calloc((size_t)n_threads, sizeof(tg_job));
+  pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+  if (!jobs || !th) {
+    free(jobs);
+    free(th);
+    return -1;
+  }
+  for (int t = 0; t < n_threads; ++t) {
+    tg_job *J = &jobs[t];
+    J->m = m;
+    J->q_obs = q_obs;
+    seed_to_key(seed, J->key);
+    J->base = base;
+    J->lo = n * (uint64_t)t / (uint64_t)n_threads;
+    J->hi = n * (uint64_t)(t + 1) / (uint64_t)n_threads;
+    J->sub = sub;
+    J->theta = theta;
+    J->summ = summ;
+    J->y = y;
+    J->uv = uv;
+    J->dist = dist;
+  }
+  for (int t = 1; t < n_threads; ++t) pthread_create(&th[t], NULL, tg_worker, &jobs[t]);
+  tg_worker(&jobs[0]);
+  int rc = jobs[0].rc;
+  for (int t = 1; t < n_threads; ++t) {
+    pthread_join(th[t], NULL);
+    if (jobs[t].rc) rc = jobs[t].rc;
+  }
+  free(jobs);
+  free(th);
+  return rc;
 }

@@ -29,6 +29,10 @@ extern "C" {
 
 #define ORC_TAG_PRIOR 0u
 #define ORC_TAG_PATH 1u
+#define ORC_TAG_BASE 2u
+#define ORC_TAG_TOGGLE_PRIOR 4u
+#define ORC_TAG_TOGGLE_PATH 5u
+#define ORC_TOGGLE_NQ 19
 
 /* OU model for ABC: dX = th1 (th2 - X) dt + th3 dW, X(0) = x0, with
  * independent uniform priors th_j ~ U(lo[j], hi[j]). */
@@ -51,6 +55,9 @@ void orc_philox_batch(uint64_t seed, const uint32_t *ctr, uint64_t n,
 
 /* The uniform that a 32-bit word encodes (see header comment). */
 double orc_u01(uint32_t w);
+
+/* Box-Muller on given word pairs: w is [n][2] (even, odd), z is [n][2]. */
+void orc_box_muller_words(const uint32_t *w, uint64_t n, double *z);
 
 /* Normals j0 .. j0+n-1 of stream (seed, c1, c2, tag): normal j comes from
  * counter block j/4, lane j%4. */
@@ -88,6 +95,39 @@ void orc_moments(const double *theta, const uint64_t *idx, uint64_t k,
 int orc_pvalue_sweep(const double *lambda, uint32_t n_lambda, uint32_t n_obs,
                      uint64_t m_sets, uint64_t base, double ybar_obs, uint64_t seed,
                      uint64_t *counts, double *p, double *ybar, int n_threads);
+
+/* Weak-informativity test (Algorithm 2) for the conjugate normal model, with
+ * the sufficient statistic ybar.  For each k < n_lambda:
+ *   base sets   i < N: ybar0 from stream (seed, i, k, BASE) with lambda_0,
+ *   lambda sets j < N: ybar  from stream (seed, j, k, PATH) with lambda_k,
+ *   p_k^i = #{j : |ybar_k^j| >= |ybar0_k^i|} / N           (indicator estimate)
+ *   gamma_k = the ceil(alpha N)-th smallest of p_k^1..p_k^N (alpha quantile).
+ * counts (nullable) is [n_lambda][N] (the numerators of p_k^i). */
+int orc_weakinf(const double *lambda, uint32_t n_lambda, double lambda0, uint32_t n_obs,
+                uint64_t n_sets, double alpha, uint64_t seed, double *gamma,
+                uint64_t *counts, int n_threads);
+
+/* Genetic toggle switch (Sec. 3.2-3.4): theta = (mu, sigma, gamma, alpha_u,
+ * alpha_v, beta_u, beta_v) with independent uniform priors on [lo, hi];
+ * C cells, each evolved over T-1 Euler-Maruyama steps (Delta t = 1) from
+ * u = v = 10, then observed with noise; summaries are the 19 quantiles at
+ * levels 0.05 .. 0.95 (linear interpolation between order statistics).
+ * Random numbers, for sample g:
+ *   prior:  blocks (0, g, sub, TOGGLE_PRIOR) words 0..3 -> theta_0..3 and
+ *           (1, g, sub, TOGGLE_PRIOR) words 0..2 -> theta_4..6;
+ *   cell c: stream (g, c, (sub << 8) | TOGGLE_PATH): normal 2(j-1) and
+ *           2(j-1)+1 drive u and v at step j = 1..T-1, normal 2(T-1) is eta. */
+typedef struct orc_toggle_model {
+  double lo[7];
+  double hi[7];
+  uint32_t T;
+  uint32_t C;
+} orc_toggle_model;
+
+/* uv (nullable) receives the final (u, v) of every cell, [n][C][2]. */
+int orc_toggle_prior_predictive(const orc_toggle_model *m, const double *q_obs, uint64_t base,
+                                uint64_t n, uint64_t seed, uint32_t sub, double *theta,
+                                double *summ, double *y, double *uv, double *dist, int n_threads);
 
 #ifdef __cplusplus
 }

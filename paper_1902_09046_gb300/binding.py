@@ -33,8 +33,17 @@ _ERRNAMES = {PPABC_EINVAL: "EINVAL", PPABC_ENOMEM: "ENOMEM", PPABC_ECUDA: "ECUDA
 
 # Every symbol include/ppabc.h declares (checked by the CPU test-suite).
 EXPORTED = ("ppabc_abi_version", "ppabc_last_error", "ppabc_device_check", "ppabc_philox_raw",
-            "ppabc_normals", "abc_prior_predictive", "abc_select_workspace_bytes", "abc_select",
-            "abc_select_static", "pvalue_sweep")
+            "ppabc_normals", "ppabc_box_muller", "abc_prior_predictive", "abc_select_workspace_bytes", "abc_select",
+            "abc_select_static", "pvalue_sweep", "ppabc_batch_workspace_bytes",
+            "ppabc_batch_prepare", "ppabc_batch_launch", "ppabc_batch_launch_graph",
+            "ppabc_batch_plan_destroy", "ppabc_batch_run", "ppabc_server_create",
+            "ppabc_server_submit", "ppabc_server_poll", "ppabc_server_wait", "ppabc_server_fetch",
+            "ppabc_server_release", "ppabc_server_cancel", "ppabc_server_get_stats",
+            "ppabc_server_now", "ppabc_server_destroy", "weakinf_test")
+WEAKINF_MAX_SETS = 16384
+PPABC_PENDING = 1
+JOB_ABC = 0
+JOB_PVALUE = 1
 STATIC_SELECT_MAX_N = 1 << 24
 
 
@@ -60,6 +69,48 @@ class OUModel(ctypes.Structure):
         o.n_steps = int(m["n_steps"])
         o.n_obs = int(m["n_obs"])
         return o
+
+
+class ABCJob(ctypes.Structure):
+    _fields_ = [("model", OUModel), ("y_obs", ctypes.c_double * PPABC_MAX_OBS),
+                ("n_samples", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("substream", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("k", ctypes.c_uint64), ("eps", ctypes.c_double),
+                ("dist", ctypes.c_void_p), ("idx_out", ctypes.c_void_p),
+                ("rec_out", ctypes.c_void_p), ("cap", ctypes.c_uint64),
+                ("n_acc_out", ctypes.c_void_p), ("eps_out", ctypes.c_void_p),
+                ("post_out", ctypes.c_void_p)]
+
+
+class TileConfig(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_uint32), ("min_tile_steps", ctypes.c_uint32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("substream", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("model", OUModel), ("y_obs", ctypes.c_double * PPABC_MAX_OBS),
+                ("n_samples", ctypes.c_uint64), ("k", ctypes.c_uint64), ("lam", ctypes.c_double),
+                ("n_obs", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("m_sets", ctypes.c_uint64), ("ybar_obs", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_int32), ("job_id", ctypes.c_uint64),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("n_acc", ctypes.c_uint64), ("eps", ctypes.c_double),
+                ("post", ctypes.c_double * 6), ("count", ctypes.c_uint64), ("p", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {"status": self.status, "kind": self.kind, "job_id": self.job_id,
+                "t_submit": self.t_submit, "t_admit": self.t_admit, "t_done": self.t_done,
+                "n_acc": self.n_acc, "eps": self.eps, "post": list(self.post),
+                "count": self.count, "p": self.p}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "completed", "failed",
+                                               "cancelled", "queued", "running",
+                                               "arena_used_bytes", "peak_arena_bytes")]
 
 
 _lock = threading.Lock()
@@ -91,11 +142,29 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
             "ppabc_device_check": ([], i32),
             "ppabc_philox_raw": ([u64, P, u64, P, P], i32),
             "ppabc_normals": ([u64, u32, u32, u32, u64, u64, P, P], i32),
+            "ppabc_box_muller": ([P, u64, P, P], i32),
             "abc_prior_predictive": ([M, P, u64, u64, u64, u32, P, P, P, P], i32),
             "abc_select_workspace_bytes": ([u64], sz),
             "abc_select": ([P, u64, u64, dbl, M, u64, u64, u32, P, P, P, u64, P, P, P, P, sz, P], i32),
             "abc_select_static": ([P, u64, u64, dbl, M, u64, u64, u32, P, P, P, u64, P, P, P, P], i32),
             "pvalue_sweep": ([P, u32, u32, u64, u64, dbl, u64, P, P, P, P], i32),
+            "ppabc_batch_workspace_bytes": ([P, u32], sz),
+            "ppabc_batch_prepare": ([P, u32, P, P, sz, P, ctypes.POINTER(P)], i32),
+            "ppabc_batch_launch": ([P, P], i32),
+            "ppabc_batch_launch_graph": ([P, P], i32),
+            "ppabc_batch_plan_destroy": ([P], i32),
+            "ppabc_batch_run": ([P, u32, P, P, sz, P], i32),
+            "ppabc_server_create": ([P, sz, u32, ctypes.POINTER(P)], i32),
+            "ppabc_server_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(u64)], i32),
+            "ppabc_server_poll": ([P, u64, ctypes.POINTER(Result)], i32),
+            "ppabc_server_wait": ([P, u64, dbl, ctypes.POINTER(Result)], i32),
+            "ppabc_server_fetch": ([P, u64, P, P, u64, ctypes.POINTER(u64)], i32),
+            "ppabc_server_release": ([P, u64], i32),
+            "ppabc_server_cancel": ([P, u64], i32),
+            "ppabc_server_get_stats": ([P, ctypes.POINTER(ServerStats)], i32),
+            "ppabc_server_now": ([P], dbl),
+            "ppabc_server_destroy": ([P], i32),
+            "weakinf_test": ([P, u32, dbl, u32, u64, dbl, u64, P, P, P], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -141,6 +210,15 @@ def philox_raw(seed: int, ctr: torch.Tensor, stream=None) -> torch.Tensor:
 def normals(seed: int, c1: int, c2: int, tag: int, j0: int, n: int, stream=None) -> torch.Tensor:
     z = torch.empty(n, dtype=torch.float32, device="cuda")
     _check(load_library().ppabc_normals(seed, c1, c2, tag, j0, n, _ptr(z), _stream(stream)))
+    return z
+
+
+def box_muller(w: torch.Tensor, stream=None) -> torch.Tensor:
+    """w: [n,2] uint32 (CUDA) -> [n,2] float32 Box-Muller normals."""
+    if w.dtype != torch.uint32 or w.dim() != 2 or w.shape[1] != 2:
+        raise ValueError("w must be a [n,2] uint32 tensor")
+    z = torch.empty(w.shape, dtype=torch.float32, device=w.device)
+    _check(load_library().ppabc_box_muller(_ptr(w), w.shape[0], _ptr(z), _stream(stream)))
     return z
 
 
@@ -268,3 +346,186 @@ def pvalue_sweep(lambdas: torch.Tensor, n_obs: int, m_sets: int, ybar_obs: float
                                        _ptr(counts), _ptr(p), _ptr(ybar if want_ybar else None),
                                        _stream(stream)))
     return {"counts": counts, "p": p, "ybar": ybar if want_ybar else None}
+
+
+def weakinf_test(lambdas: torch.Tensor, lambda0: float, n_obs: int, n_sets: int, alpha: float,
+                 seed: int, want_counts: bool = False, stream=None) -> dict:
+    """Algorithm 2's alpha-level cut-offs gamma [K] (and counts [K,N] uint32)."""
+    K = lambdas.shape[0]
+    gamma = torch.empty(K, dtype=torch.float64, device=lambdas.device)
+    counts = (torch.empty((K, n_sets), dtype=torch.uint32, device=lambdas.device)
+              if want_counts else None)
+    _check(load_library().weakinf_test(_ptr(lambdas), K, float(lambda0), n_obs, n_sets,
+                                       float(alpha), seed, _ptr(gamma), _ptr(counts),
+                                       _stream(stream)))
+    return {"gamma": gamma, "counts": counts}
+
+
+# ---------------------------------------------------------------------------
+# Batched jobs
+# ---------------------------------------------------------------------------
+
+class Batch:
+    """A prepared batch of OU-ABC jobs (persistent launch + per-job selection).
+
+    ``jobs`` is a list of dicts with keys model, y_obs, n_samples, seed and
+    either k or eps (optionally substream, cap).  Output tensors per job are
+    allocated here and returned by :meth:`results`."""
+
+    def __init__(self, jobs: list[dict], tile: tuple[int, int] | None = None, stream=None,
+                 device=None):
+        self.lib = load_library()
+        dev = torch.device(device or "cuda")
+        n = len(jobs)
+        self.arr = (ABCJob * max(n, 1))()
+        self.outs = []
+        for j, spec in enumerate(jobs):
+            J = self.arr[j]
+            J.model = OUModel.from_dict(spec["model"])
+            y = [float(v) for v in (spec["y_obs"].tolist() if hasattr(spec["y_obs"], "tolist")
+                                    else spec["y_obs"])]
+            for i, v in enumerate(y):
+                J.y_obs[i] = v
+            J.n_samples = int(spec["n_samples"])
+            J.seed = int(spec["seed"])
+            J.substream = int(spec.get("substream", 0))
+            J.k = int(spec.get("k", 0))
+            J.eps = float(spec.get("eps", math.inf))
+            cap = int(spec.get("cap", J.k if J.k > 0 else J.n_samples))
+            o = {"idx": torch.empty(max(cap, 1), dtype=torch.uint32, device=dev),
+                 "rec": torch.empty((max(cap, 1), 4), dtype=torch.float32, device=dev),
+                 "n_acc": torch.empty(1, dtype=torch.uint64, device=dev),
+                 "eps": torch.empty(1, dtype=torch.float64, device=dev),
+                 "post": torch.empty(6, dtype=torch.float64, device=dev),
+                 "cap": cap}
+            if spec.get("keep_dist"):
+                o["dist"] = torch.empty(J.n_samples, dtype=torch.float64, device=dev)
+                J.dist = o["dist"].data_ptr()
+            J.idx_out, J.rec_out, J.cap = o["idx"].data_ptr(), o["rec"].data_ptr(), cap
+            J.n_acc_out, J.eps_out, J.post_out = (o["n_acc"].data_ptr(), o["eps"].data_ptr(),
+                                                  o["post"].data_ptr())
+            self.outs.append(o)
+        self.n = n
+        ws_bytes = int(self.lib.ppabc_batch_workspace_bytes(self.arr, n))
+        self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        self.cfg = TileConfig(*(tile or (128, 4096)))
+        self.plan = ctypes.c_void_p()
+        _check(self.lib.ppabc_batch_prepare(self.arr, n, ctypes.byref(self.cfg), _ptr(self.ws),
+                                            ws_bytes, _stream(stream), ctypes.byref(self.plan)))
+
+    def launch(self, graph: bool = False, stream=None) -> None:
+        fn = self.lib.ppabc_batch_launch_graph if graph else self.lib.ppabc_batch_launch
+        _check(fn(self.plan, _stream(stream)))
+
+    def results(self) -> list[dict]:
+        return [{k: (v[:o["cap"]] if k in ("idx", "rec") else v) for k, v in o.items() if k != "cap"}
+                for o in self.outs]
+
+    def close(self) -> None:
+        if self.plan:
+            self.lib.ppabc_batch_plan_destroy(self.plan)
+            self.plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# Request server
+# ---------------------------------------------------------------------------
+
+def abc_request(model: dict, y_obs, n_samples: int, k: int, seed: int, substream: int = 0) -> Request:
+    r = Request()
+    r.kind = JOB_ABC
+    r.substream = substream
+    r.seed = seed
+    r.model = OUModel.from_dict(model)
+    for i, v in enumerate(y_obs.tolist() if hasattr(y_obs, "tolist") else y_obs):
+        r.y_obs[i] = float(v)
+    r.n_samples = n_samples
+    r.k = k
+    return r
+
+
+def pvalue_request(lam: float, n_obs: int, m_sets: int, ybar_obs: float, seed: int) -> Request:
+    r = Request()
+    r.kind = JOB_PVALUE
+    r.seed = seed
+    r.lam = lam
+    r.n_obs = n_obs
+    r.m_sets = m_sets
+    r.ybar_obs = ybar_obs
+    return r
+
+
+class Server:
+    """Continuous-batching request server over an arena of device memory."""
+
+    def __init__(self, arena_bytes: int, n_slots: int = 8, device=None):
+        self.lib = load_library()
+        self.arena = torch.empty(arena_bytes, dtype=torch.uint8, device=device or "cuda")
+        self.h = ctypes.c_void_p()
+        _check(self.lib.ppabc_server_create(_ptr(self.arena), arena_bytes, n_slots,
+                                            ctypes.byref(self.h)))
+
+    def submit(self, req: Request) -> int:
+        jid = ctypes.c_uint64()
+        _check(self.lib.ppabc_server_submit(self.h, ctypes.byref(req), ctypes.byref(jid)))
+        return jid.value
+
+    def poll(self, job_id: int) -> dict | None:
+        res = Result()
+        rc = self.lib.ppabc_server_poll(self.h, job_id, ctypes.byref(res))
+        if rc == PPABC_PENDING:
+            return None
+        _check(rc)
+        return res.as_dict()
+
+    def wait(self, job_id: int, timeout_s: float = 60.0) -> dict:
+        res = Result()
+        _check(self.lib.ppabc_server_wait(self.h, job_id, timeout_s, ctypes.byref(res)))
+        return res.as_dict()
+
+    def fetch(self, job_id: int, cap: int):
+        import numpy as np
+        idx = np.zeros(max(cap, 1), dtype=np.uint32)
+        rec = np.zeros((max(cap, 1), 4), dtype=np.float32)
+        n = ctypes.c_uint64()
+        _check(self.lib.ppabc_server_fetch(self.h, job_id, idx.ctypes.data_as(ctypes.c_void_p),
+                                           rec.ctypes.data_as(ctypes.c_void_p), cap,
+                                           ctypes.byref(n)))
+        return idx[:n.value], rec[:n.value]
+
+    def release(self, job_id: int) -> None:
+        _check(self.lib.ppabc_server_release(self.h, job_id))
+
+    def cancel(self, job_id: int) -> None:
+        _check(self.lib.ppabc_server_cancel(self.h, job_id))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self.lib.ppabc_server_get_stats(self.h, ctypes.byref(st)))
+        return {n: getattr(st, n) for n, _ in ServerStats._fields_}
+
+    def now(self) -> float:
+        return float(self.lib.ppabc_server_now(self.h))
+
+    def close(self) -> None:
+        if self.h:
+            self.lib.ppabc_server_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

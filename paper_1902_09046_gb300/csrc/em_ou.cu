@@ -50,29 +50,45 @@ cudaError_t launch_em_ou(const OUConst& P, uint64_t base, uint32_t n, float* the
 // ---------------------------------------------------------------------------
 // Raw generator outputs (parity hooks for the RNG itself).
 // ---------------------------------------------------------------------------
-__global__ void philox_raw_kernel(uint32_t k0, uint32_t k1, const uint4* __restrict__ ctr,
+__global__ void philox_raw_kernel(const __grid_constant__ PhiloxKeys K, const uint4* __restrict__ ctr,
                                   uint64_t n, uint4* __restrict__ out) {
   const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
+  if (i < n) out[i] = philox4x32_10(ctr[i], K);
 }
 
-__global__ void normals_kernel(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t tag,
-                               uint64_t j0, uint64_t n, float* __restrict__ z) {
+__global__ void normals_kernel(const __grid_constant__ PhiloxKeys K, uint32_t c1, uint32_t c2,
+                               uint32_t tag, uint64_t j0, uint64_t n, float* __restrict__ z) {
   const uint64_t t = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const uint64_t j = j0 + t;
-  const float4 q = block_normals(static_cast<uint32_t>(j >> 2), c1, c2, tag, k0, k1);
+  const PhiloxStream S = philox_stream(K, c1, c2, tag);
+  const float4 q = normals_of(philox_block(S, K, static_cast<uint32_t>(j >> 2)));
   const uint32_t lane = static_cast<uint32_t>(j & 3u);
   z[t] = lane == 0 ? q.x : lane == 1 ? q.y : lane == 2 ? q.z : q.w;
+}
+
+__global__ void box_muller_kernel(const uint2* __restrict__ w, uint64_t n, float2* __restrict__ z) {
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint2 p = w[i];
+  float2 q;
+  box_muller(p.x, p.y, q.x, q.y);
+  z[i] = q;
+}
+
+cudaError_t launch_box_muller(const uint32_t* w, uint64_t n, float* z, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
+  box_muller_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const uint2*>(w), n,
+                                           reinterpret_cast<float2*>(z));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_philox_raw(uint64_t seed, const uint32_t* ctr, uint64_t n, uint32_t* out,
                               cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
-  philox_raw_kernel<<<blocks, 256, 0, s>>>(static_cast<uint32_t>(seed),
-                                           static_cast<uint32_t>(seed >> 32),
-                                           reinterpret_cast<const uint4*>(ctr), n,
+  philox_raw_kernel<<<blocks, 256, 0, s>>>(philox_keys(seed), reinterpret_cast<const uint4*>(ctr), n,
                                            reinterpret_cast<uint4*>(out));
   return cudaGetLastError();
 }
@@ -81,8 +97,7 @@ cudaError_t launch_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag
                            uint64_t n, float* z, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
-  normals_kernel<<<blocks, 256, 0, s>>>(static_cast<uint32_t>(seed),
-                                        static_cast<uint32_t>(seed >> 32), c1, c2, tag, j0, n, z);
+  normals_kernel<<<blocks, 256, 0, s>>>(philox_keys(seed), c1, c2, tag, j0, n, z);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@ cudaError_t launch_philox_raw(uint64_t seed, const uint32_t* ctr, uint64_t n, ui
                               cudaStream_t s);
 cudaError_t launch_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag, uint64_t j0,
                            uint64_t n, float* z, cudaStream_t s);
+cudaError_t launch_box_muller(const uint32_t* w, uint64_t n, float* z, cudaStream_t s);
 cudaError_t launch_em_ou(const OUConst& P, uint64_t base, uint32_t n, float* theta_out,
                          double* summ_out, double* dist_out, cudaStream_t s);
 
@@ -41,5 +42,10 @@ cudaError_t launch_pvalue(const double* lambda, uint32_t n_lambda, uint32_t n_ob
                           uint32_t m_sets, uint32_t set_base, double ybar_obs, uint64_t seed,
                           uint64_t* counts,
                           double* p_out, double* ybar_out, cudaStream_t s);
+
+// Weak-informativity test.
+cudaError_t launch_weakinf(const double* lambda, uint32_t n_lambda, double lambda0, uint32_t n_obs,
+                           uint32_t n_sets, double alpha, uint64_t seed, double* gamma_out,
+                           uint32_t* counts_out, cudaStream_t s);
 
 }  // namespace ppabc

@@ -34,8 +34,8 @@ struct OUConst {
   float x0;
   uint32_t n_steps;
   uint32_t n_obs;
-  uint32_t key0, key1;
   uint32_t sub;
+  PhiloxKeys keys;
   uint32_t s_obs[PPABC_MAX_OBS];
   double y[PPABC_MAX_OBS];
 };
@@ -43,25 +43,26 @@ struct OUConst {
 // Prior draw of sample g: th_j = lo_j + span_j u(w_j).
 __device__ __forceinline__ void ou_prior(const OUConst& P, uint32_t g, float& th1, float& th2,
                                          float& th3) {
-  const uint4 w = philox4x32_10(make_uint4(0u, g, P.sub, kTagPrior), P.key0, P.key1);
+  const uint4 w = philox4x32_10(make_uint4(0u, g, P.sub, kTagPrior), P.keys);
   th1 = fmaf(P.span[0], u01f(w.x), P.lo[0]);
   th2 = fmaf(P.span[1], u01f(w.y), P.lo[1]);
   th3 = fmaf(P.span[2], u01f(w.z), P.lo[2]);
 }
 
-// One Euler-Maruyama step with a Kahan-compensated state:
-// inc = k (th2 - X) + c xi, then X <- X + inc with the rounding error kept in comp.
-__device__ __forceinline__ void em_step(float& X, float& comp, float k, float th2, float c,
-                                        float xi) {
-  const float inc = fmaf(k, th2 - X, c * xi);
-  const float y = inc - comp;
-  const float t = X + y;
-  comp = (t - X) - y;
-  X = t;
+// One Euler-Maruyama step on the centred state Y = X - th2 with Kahan
+// compensation: Y <- Y - k Y + c xi, with c xi already folded into `cz`;
+// Y - comp is the running value and comp holds the rounding error.
+__device__ __forceinline__ void em_step(float& Y, float& comp, float k, float cz) {
+  const float y = fmaf(-k, Y, cz) - comp;
+  const float t = Y + y;
+  comp = (t - Y) - y;
+  Y = t;
 }
 
 // Simulate sample g and return rho; the summaries go to summ[j * summ_stride]
-// when summ is non-null.
+// when summ is non-null.  X_s = th2 + Y_s with Y_0 = x0 - th2 split exactly
+// into (Y, -comp); observation steps are handled between runs of whole
+// 4-step counter blocks, which take no per-step test.
 template <bool kWantSumm>
 __device__ __forceinline__ double ou_path(const OUConst& P, uint32_t g, float th1, float th2,
                                           float th3, double* summ, uint32_t summ_stride) {
@@ -69,36 +70,50 @@ __device__ __forceinline__ double ou_path(const OUConst& P, uint32_t g, float th
   const float c = th3 * P.sqrt_dt;
   const uint32_t S = P.n_steps;
   const uint32_t n_obs = P.n_obs;
-  float X = P.x0;
-  float comp = 0.0f;
+  // Y0 = x0 - th2 exactly as Y - comp (Knuth's two-sum).
+  float Y = P.x0 - th2;
+  float comp;
+  {
+    const float bb = Y - P.x0;
+    const float err = (P.x0 - (Y - bb)) + (-th2 - bb);
+    comp = -err;
+  }
+  const double th2d = static_cast<double>(th2);
   double acc = 0.0;
-  uint32_t j = 0;
-  uint32_t s_next = P.s_obs[0];
-  uint32_t s = 0;  // steps taken
-  for (uint32_t b = 0; s < S; ++b) {
-    const float4 z = block_normals(b, g, P.sub, kTagPath, P.key0, P.key1);
-    if (s + 4u < s_next) {
-      // No observation among steps s+1 .. s+4 (uniform across the launch).
-      em_step(X, comp, k, th2, c, z.x);
-      em_step(X, comp, k, th2, c, z.y);
-      em_step(X, comp, k, th2, c, z.z);
-      em_step(X, comp, k, th2, c, z.w);
-      s += 4u;
-    } else {
-      const float zz[4] = {z.x, z.y, z.z, z.w};
+  const PhiloxStream stream = philox_stream(P.keys, g, P.sub, kTagPath);
+  uint32_t s = 0;  // steps taken (4 b except inside the last block)
+  uint32_t b = 0;  // next counter block
+  uint32_t j = 0;  // next observation
+  while (j < n_obs) {
+    uint32_t s_next = P.s_obs[j];  // > s
+    // Whole blocks (steps s+1 .. s+4) that end before the observation step;
+    // the count is the same for every thread of a launch.
+    const uint32_t b_end = b + (s_next > s + 4u ? (s_next - s - 1u) >> 2 : 0u);
+    s += (b_end - b) << 2;
+#pragma unroll 2
+    for (; b < b_end; ++b) {
+      const float4 z = scaled_normals_of(philox_block(stream, P.keys, b), c);
+      em_step(Y, comp, k, z.x);
+      em_step(Y, comp, k, z.y);
+      em_step(Y, comp, k, z.z);
+      em_step(Y, comp, k, z.w);
+    }
+    // The block holding step s_next (and possibly later observation steps).
+    const float4 z = scaled_normals_of(philox_block(stream, P.keys, b), c);
+    ++b;
+    const float zz[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        if (s < S) {
-          em_step(X, comp, k, th2, c, zz[l]);
-          ++s;
-          if (s == s_next) {
-            const double x = static_cast<double>(X) - static_cast<double>(comp);
-            const double r = x - P.y[j];
-            acc = fma(r, r, acc);
-            if (kWantSumm) summ[static_cast<size_t>(j) * summ_stride] = x;
-            ++j;
-            s_next = (j < n_obs) ? P.s_obs[j] : 0xFFFFFFFFu;
-          }
+    for (int l = 0; l < 4; ++l) {
+      if (s < S) {
+        em_step(Y, comp, k, zz[l]);
+        ++s;
+        if (s == s_next) {
+          const double x = th2d + (static_cast<double>(Y) - static_cast<double>(comp));
+          const double r = x - P.y[j];
+          acc = fma(r, r, acc);
+          if (kWantSumm) summ[static_cast<size_t>(j) * summ_stride] = x;
+          ++j;
+          s_next = (j < n_obs) ? P.s_obs[j] : 0xFFFFFFFFu;
         }
       }
     }

@@ -66,6 +66,7 @@ int validate_model(const ppabc_ou_model* m) {
   if (m->n_obs < 1 || m->n_obs > PPABC_MAX_OBS)
     return set_error(PPABC_EINVAL, "n_obs must be in [1, %d]", PPABC_MAX_OBS);
   if (m->n_steps < m->n_obs) return set_error(PPABC_EINVAL, "n_steps must be >= n_obs");
+  if (m->n_steps > 0x80000000u) return set_error(PPABC_EINVAL, "n_steps must be <= 2^31");
   return PPABC_OK;
 }
 
@@ -84,8 +85,7 @@ int make_ou_const(const ppabc_ou_model* m, const double* h_y_obs, uint64_t seed,
   P.x0 = static_cast<float>(m->x0);
   P.n_steps = m->n_steps;
   P.n_obs = m->n_obs;
-  P.key0 = static_cast<uint32_t>(seed);
-  P.key1 = static_cast<uint32_t>(seed >> 32);
+  P.keys = philox_keys(seed);
   P.sub = substream;
   for (uint32_t j = 1; j <= m->n_obs; ++j)
     P.s_obs[j - 1] = static_cast<uint32_t>((static_cast<uint64_t>(j) * m->n_steps) / m->n_obs);
@@ -132,6 +132,17 @@ int ppabc_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag, uint64_
   if (rc) return rc;
   return check_cuda(launch_normals(seed, c1, c2, tag, j0, n, z, static_cast<cudaStream_t>(stream)),
                     "normals launch");
+}
+
+int ppabc_box_muller(const uint32_t* w, uint64_t n, float* z, void* stream) {
+  if (n == 0) return PPABC_OK;
+  if (!w || !z) return set_error(PPABC_EINVAL, "w and z must be non-NULL");
+  if ((reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(z)) & 7u)
+    return set_error(PPABC_EINVAL, "w and z must be 8-byte aligned");
+  if (n > 0x7FFFFFFFull * 256ull) return set_error(PPABC_EINVAL, "n too large");
+  int rc = require_device();
+  if (rc) return rc;
+  return check_cuda(launch_box_muller(w, n, z, static_cast<cudaStream_t>(stream)), "box_muller launch");
 }
 
 int abc_prior_predictive(const ppabc_ou_model* h_model, const double* h_y_obs, uint64_t n_samples,
@@ -209,6 +220,24 @@ int pvalue_sweep(const double* lambda, uint32_t n_lambda, uint32_t n_obs, uint64
                                   static_cast<uint32_t>(set_base), ybar_obs, seed, counts, p_out,
                                   ybar_out, static_cast<cudaStream_t>(stream)),
                     "pvalue_sweep launch");
+}
+
+int weakinf_test(const double* lambda, uint32_t n_lambda, double lambda0, uint32_t n_obs,
+                 uint64_t n_sets, double alpha, uint64_t seed, double* gamma_out, uint32_t* counts_out,
+                 void* stream) {
+  if (n_lambda == 0) return PPABC_OK;
+  if (n_lambda > 0x7FFFFFFFu) return set_error(PPABC_EINVAL, "n_lambda too large");
+  if (!lambda || !gamma_out) return set_error(PPABC_EINVAL, "lambda and gamma_out must be non-NULL");
+  if (n_obs < 1) return set_error(PPABC_EINVAL, "n_obs must be >= 1");
+  if (n_sets < 1 || n_sets > PPABC_WEAKINF_MAX_SETS)
+    return set_error(PPABC_EINVAL, "n_sets must be in [1, %d]", PPABC_WEAKINF_MAX_SETS);
+  if (!(alpha > 0.0 && alpha <= 1.0)) return set_error(PPABC_EINVAL, "alpha must be in (0, 1]");
+  if (!isfinite(lambda0) || lambda0 < 0.0) return set_error(PPABC_EINVAL, "lambda0 must be >= 0");
+  int rc = require_device();
+  if (rc) return rc;
+  return check_cuda(launch_weakinf(lambda, n_lambda, lambda0, n_obs, static_cast<uint32_t>(n_sets), alpha,
+                                   seed, gamma_out, counts_out, static_cast<cudaStream_t>(stream)),
+                    "weakinf launch");
 }
 
 }  // extern "C"

@@ -7,10 +7,10 @@
 //   counts[k] += [|ybar| >= |ybar_obs|].
 // One thread walks a strided set of data sets of one lambda (blockIdx.y) and
 // keeps its count in a register; a warp reduction and one 64-bit atomic per
-// warp add it to counts[k].  The normals are binary32 and summed with Kahan
-// compensation; ybar and the comparison are binary64 (a handful of binary64
-// operations per data set, against 51 normals of binary32 work).
+// warp add it to counts[k].  ybar comes from dataset_ybar (binary32 normals,
+// Kahan-compensated sum, binary64 ybar); the comparison is binary64.
 #include "internal.h"
+#include "ybar.cuh"
 
 namespace ppabc {
 
@@ -18,54 +18,23 @@ namespace {
 
 constexpr int kPvThreads = 256;
 
-__device__ __forceinline__ void kahan_add(float& s, float& comp, float x) {
-  const float y = x - comp;
-  const float t = s + y;
-  comp = (t - s) - y;
-  s = t;
-}
-
 template <bool kWantYbar>
 __global__ void __launch_bounds__(kPvThreads) pvalue_tail(const double* __restrict__ lambda,
                                                           uint32_t n_obs, double inv_n,
                                                           uint32_t m_sets, uint32_t set_base,
                                                           double abs_ybar_obs,
-                                                          uint32_t k0, uint32_t k1,
+                                                          const __grid_constant__ PhiloxKeys K,
                                                           unsigned long long* __restrict__ counts,
                                                           double* __restrict__ ybar_out) {
   const uint32_t k = blockIdx.y;
   const double lam = lambda[k];
-  const uint32_t n_full = (n_obs + 1) >> 2;  // counter blocks whose 4 normals are all used
-  const uint32_t rem = (n_obs + 1) & 3u;     // normals used from the last block
   unsigned int count = 0;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kPvThreads;
   for (uint64_t m0 = static_cast<uint64_t>(blockIdx.x) * kPvThreads; m0 < m_sets; m0 += stride) {
     const uint64_t m = m0 + threadIdx.x;
     if (m < m_sets) {
-      float z0 = 0.0f, s = 0.0f, comp = 0.0f;
-      for (uint32_t b = 0; b < n_full; ++b) {
-        const float4 z = block_normals(b, set_base + static_cast<uint32_t>(m), k, kTagPath, k0, k1);
-        if (b == 0) {
-          z0 = z.x;
-        } else {
-          kahan_add(s, comp, z.x);
-        }
-        kahan_add(s, comp, z.y);
-        kahan_add(s, comp, z.z);
-        kahan_add(s, comp, z.w);
-      }
-      if (rem) {
-        const float4 z = block_normals(n_full, set_base + static_cast<uint32_t>(m), k, kTagPath, k0, k1);
-        if (n_full == 0) {
-          z0 = z.x;
-        } else {
-          kahan_add(s, comp, z.x);
-        }
-        if (rem > 1) kahan_add(s, comp, z.y);
-        if (rem > 2) kahan_add(s, comp, z.z);
-      }
-      const double sum = static_cast<double>(s) - static_cast<double>(comp);
-      const double ybar = fma(lam, static_cast<double>(z0), sum * inv_n);
+      const double ybar = dataset_ybar(K, lam, n_obs, inv_n, set_base + static_cast<uint32_t>(m), k,
+                                       kTagPath);
       if (kWantYbar) ybar_out[static_cast<size_t>(k) * m_sets + m] = ybar;
       count += (fabs(ybar) >= abs_ybar_obs) ? 1u : 0u;
     }
@@ -99,15 +68,15 @@ cudaError_t launch_pvalue(const double* lambda, uint32_t n_lambda, uint32_t n_ob
   if (bx > need) bx = need;
   if (bx < 1) bx = 1;
   const dim3 grid(static_cast<unsigned>(bx), n_lambda);
-  const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+  const PhiloxKeys K = philox_keys(seed);
   const double inv_n = 1.0 / static_cast<double>(n_obs);
   const double a = fabs(ybar_obs);
   auto* c = reinterpret_cast<unsigned long long*>(counts);
   if (ybar_out)
-    pvalue_tail<true><<<grid, kPvThreads, 0, s>>>(lambda, n_obs, inv_n, m_sets, set_base, a, k0, k1, c,
+    pvalue_tail<true><<<grid, kPvThreads, 0, s>>>(lambda, n_obs, inv_n, m_sets, set_base, a, K, c,
                                                    ybar_out);
   else
-    pvalue_tail<false><<<grid, kPvThreads, 0, s>>>(lambda, n_obs, inv_n, m_sets, set_base, a, k0, k1, c,
+    pvalue_tail<false><<<grid, kPvThreads, 0, s>>>(lambda, n_obs, inv_n, m_sets, set_base, a, K, c,
                                                     ybar_out);
   e = cudaGetLastError();
   if (e != cudaSuccess || !p_out) return e;

@@ -93,9 +93,10 @@ __global__ void select_init(SelState* st, unsigned int* hist, unsigned long long
   }
 }
 
-// Block-wide exclusive scan of one unsigned value per thread (blockDim.x = 256).
+// Block-wide exclusive scan of one unsigned value per thread (any blockDim.x
+// that is a multiple of 32, up to 1024; smem holds one value per warp).
 template <typename T>
-__device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* smem /* >= 8 */) {
+__device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* smem /* >= warps */) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T x = v;
 #pragma unroll
@@ -108,7 +109,7 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* smem /* >= 8
   if (warp == 0) {
     T w = (lane < (blockDim.x >> 5)) ? smem[lane] : T(0);
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
+    for (int o = 1; o < 32; o <<= 1) {
       const T y = __shfl_up_sync(0xFFFFFFFFu, w, o);
       if (lane >= o) w += y;
     }
@@ -457,6 +458,138 @@ __global__ void __launch_bounds__(kTileThreads) select_moments(const MomentPart*
   }
 }
 
+// ---------------------------------------------------------------------------
+// Small inputs (n <= kSmallMax): the whole selection in one CTA.  Keys and
+// indices are bitonic-sorted in shared memory (ties by index), the accepted
+// samples are flagged by index, then compacted in index order; the moments
+// are a fixed-order block reduction.  One launch instead of eleven matters
+// for the many small jobs of a serving mix.
+// ---------------------------------------------------------------------------
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallMax = 4096;
+constexpr int kSmallPer = kSmallMax / kSmallThreads;
+
+template <typename T>
+__device__ __forceinline__ T block_sum_fixed(T v, T* red /* >= 32 */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  T t = 0;
+  for (int w = 0; w < kSmallThreads / 32; ++w) t += red[w];
+  return t;
+}
+
+template <bool kTheta>
+__global__ void __launch_bounds__(kSmallThreads) select_small(
+    const double* __restrict__ dist, uint32_t n, uint32_t P, unsigned long long k, bool threshold,
+    unsigned long long cut_thr, double eps_thr, const __grid_constant__ OUConst prm, uint32_t base,
+    const float* __restrict__ theta, uint32_t* __restrict__ idx_out, float4* __restrict__ rec_out,
+    unsigned long long cap, unsigned long long* __restrict__ n_acc_out, double* __restrict__ eps_out,
+    double* __restrict__ post_out) {
+  extern __shared__ unsigned long long sm_keys[];  // P keys, then P indices, then n flags
+  uint32_t* sm_idx = reinterpret_cast<uint32_t*>(sm_keys + P);
+  unsigned char* sm_flag = reinterpret_cast<unsigned char*>(sm_idx + P);
+  __shared__ unsigned int scan_smem[kSmallThreads / 32];
+  __shared__ double red[kSmallThreads / 32];
+  for (uint32_t i = threadIdx.x; i < P; i += kSmallThreads) {
+    sm_keys[i] = i < n ? dist_key(dist[i]) : 0xFFFFFFFFFFFFFFFFull;
+    sm_idx[i] = i < n ? i : 0xFFFFFFFFu;
+    if (i < n) sm_flag[i] = 0;
+  }
+  __syncthreads();
+  if (!threshold) {
+    for (uint32_t size = 2; size <= P; size <<= 1) {
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t t = threadIdx.x; t < (P >> 1); t += kSmallThreads) {
+          const uint32_t lo = 2 * t - (t & (stride - 1));
+          const uint32_t hi = lo + stride;
+          const bool up = (lo & size) == 0;
+          const unsigned long long ka = sm_keys[lo], kb = sm_keys[hi];
+          const uint32_t ia = sm_idx[lo], ib = sm_idx[hi];
+          const bool greater = ka > kb || (ka == kb && ia > ib);
+          if (greater == up) {
+            sm_keys[lo] = kb;
+            sm_keys[hi] = ka;
+            sm_idx[lo] = ib;
+            sm_idx[hi] = ia;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (uint32_t t = threadIdx.x; t < k; t += kSmallThreads) sm_flag[sm_idx[t]] = 1;
+  } else {
+    for (uint32_t i = threadIdx.x; i < n; i += kSmallThreads) sm_flag[i] = sm_keys[i] <= cut_thr;
+  }
+  __syncthreads();
+  // Compaction in index order: thread t owns indices 4t .. 4t+3.
+  unsigned int flags = 0;
+#pragma unroll
+  for (int q = 0; q < kSmallPer; ++q) {
+    const uint32_t i = threadIdx.x * kSmallPer + q;
+    if (i < n && sm_flag[i]) flags |= 1u << q;
+  }
+  unsigned int total;
+  const unsigned int pos0 = block_exclusive_scan<unsigned int>(__popc(flags), &total, scan_smem);
+  float th[kSmallPer][3];
+  double sum[3] = {0.0, 0.0, 0.0};
+  unsigned long long pos = pos0;
+#pragma unroll
+  for (int q = 0; q < kSmallPer; ++q) {
+    if (flags & (1u << q)) {
+      const uint32_t i = threadIdx.x * kSmallPer + q;
+      float a, b, c;
+      if (kTheta) {
+        a = theta[i];
+        b = theta[static_cast<size_t>(n) + i];
+        c = theta[2 * static_cast<size_t>(n) + i];
+      } else {
+        ou_prior(prm, base + i, a, b, c);
+      }
+      th[q][0] = a;
+      th[q][1] = b;
+      th[q][2] = c;
+      sum[0] += a;
+      sum[1] += b;
+      sum[2] += c;
+      if (pos < cap) {
+        idx_out[pos] = i;
+        rec_out[pos] = make_float4(a, b, c, static_cast<float>(dist[i]));
+      }
+      ++pos;
+    }
+  }
+  double mean[3], var[3];
+  for (int d = 0; d < 3; ++d) {
+    const double tsum = block_sum_fixed<double>(sum[d], red);
+    mean[d] = total ? tsum / static_cast<double>(total) : 0.0;
+  }
+  for (int d = 0; d < 3; ++d) {
+    double m2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < kSmallPer; ++q) {
+      if (flags & (1u << q)) {
+        const double r = static_cast<double>(th[q][d]) - mean[d];
+        m2 = fma(r, r, m2);
+      }
+    }
+    var[d] = block_sum_fixed<double>(m2, red);
+  }
+  if (threadIdx.x == 0) {
+    *n_acc_out = total;
+    if (eps_out) *eps_out = threshold ? eps_thr : key_to_double(sm_keys[k - 1]);
+    if (post_out) {
+      for (int d = 0; d < 3; ++d) {
+        post_out[d] = total > 0 ? mean[d] : nan("");
+        post_out[3 + d] = total > 1 ? var[d] / static_cast<double>(total - 1) : nan("");
+      }
+    }
+  }
+}
+
 unsigned long long host_dist_key(double d) {
   if (d != d) return 0xFFFFFFFFFFFFFFFFull;
   unsigned long long b;
@@ -470,9 +603,35 @@ unsigned long long host_dist_key(double d) {
 size_t select_workspace_bytes(uint64_t n) { return WsLayout(n).total; }
 
 cudaError_t launch_select(const double* dist, uint32_t n, uint64_t k, double eps,
-                          const OUConst& P, uint64_t base, const float* theta, uint32_t* idx_out,
+                          const OUConst& P_, uint64_t base, const float* theta, uint32_t* idx_out,
                           float* rec_out, uint64_t cap, uint64_t* n_acc_out, double* eps_out,
                           double* post_out, void* ws, cudaStream_t s) {
+  const bool threshold = (k == 0);
+  if (n > 0 && n <= static_cast<uint32_t>(kSmallMax)) {
+    uint32_t P = 2;
+    while (P < n) P <<= 1;
+    const size_t smem = P * (sizeof(unsigned long long) + sizeof(uint32_t)) + ((n + 15) & ~15u);
+    const unsigned long long cut = threshold ? host_dist_key(eps) : 0ull;
+    cudaError_t e;
+    if (theta) {
+      e = cudaFuncSetAttribute(select_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(smem));
+      if (e != cudaSuccess) return e;
+      select_small<true><<<1, kSmallThreads, smem, s>>>(
+          dist, n, P, k, threshold, cut, eps, P_, static_cast<uint32_t>(base), theta, idx_out,
+          reinterpret_cast<float4*>(rec_out), cap, reinterpret_cast<unsigned long long*>(n_acc_out),
+          eps_out, post_out);
+    } else {
+      e = cudaFuncSetAttribute(select_small<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(smem));
+      if (e != cudaSuccess) return e;
+      select_small<false><<<1, kSmallThreads, smem, s>>>(
+          dist, n, P, k, threshold, cut, eps, P_, static_cast<uint32_t>(base), theta, idx_out,
+          reinterpret_cast<float4*>(rec_out), cap, reinterpret_cast<unsigned long long*>(n_acc_out),
+          eps_out, post_out);
+    }
+    return cudaGetLastError();
+  }
   const WsLayout L(n);
   char* w = static_cast<char*>(ws);
   SelState* st = reinterpret_cast<SelState*>(w + L.state);
@@ -482,7 +641,6 @@ cudaError_t launch_select(const double* dist, uint32_t n, uint64_t k, double eps
   unsigned int* tile_off = reinterpret_cast<unsigned int*>(w + L.tile_off);
   MomentPart* parts = reinterpret_cast<MomentPart*>(w + L.parts);
   const uint32_t tiles = static_cast<uint32_t>((static_cast<uint64_t>(n) + kTile - 1) / kTile);
-  const bool threshold = (k == 0);
   const unsigned long long cut_thr = threshold ? host_dist_key(eps) : 0ull;
 
   select_init<<<1, kHistThreads, 0, s>>>(st, hist, k);
@@ -505,11 +663,11 @@ cudaError_t launch_select(const double* dist, uint32_t n, uint64_t k, double eps
   if (tiles > 0) {
     if (theta)
       select_write<true><<<tiles, kTileThreads, 0, s>>>(
-          dist, n, st, threshold, cut_thr, tile_eq, tile_off, P, static_cast<uint32_t>(base), theta,
+          dist, n, st, threshold, cut_thr, tile_eq, tile_off, P_, static_cast<uint32_t>(base), theta,
           idx_out, reinterpret_cast<float4*>(rec_out), cap, parts);
     else
       select_write<false><<<tiles, kTileThreads, 0, s>>>(
-          dist, n, st, threshold, cut_thr, tile_eq, tile_off, P, static_cast<uint32_t>(base), theta,
+          dist, n, st, threshold, cut_thr, tile_eq, tile_off, P_, static_cast<uint32_t>(base), theta,
           idx_out, reinterpret_cast<float4*>(rec_out), cap, parts);
   }
   if (post_out) select_moments<<<1, kTileThreads, 0, s>>>(parts, tiles, post_out);

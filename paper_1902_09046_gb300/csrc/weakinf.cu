@@ -1,0 +1,148 @@
+// weakinf.cu -- weak-informativity test (Algorithm 2) for the conjugate model.
+//
+// For each hyperparameter lambda_k (Sec. 4.1, Eq. 8 and Eq. 9), Algorithm 2
+// draws N data sets from the base prior predictive (lambda_0) and N from the
+// lambda_k prior predictive, estimates the p-value of every base data set
+// under lambda_k as the fraction of lambda_k data sets whose prior-predictive
+// density is no larger, and returns the alpha quantile of those p-values.
+// With the sufficient statistic ybar (density falling in |ybar|) the count
+// for base set i is #{j : |ybar_k^j| >= |ybar_0^i|}.
+//
+// One CTA per lambda_k: the N values |ybar_k^j| are drawn into shared memory
+// and bitonic-sorted there, every base set's count is a binary search, and
+// the ceil(alpha N)-th smallest count comes from a shared histogram of the
+// counts.  The paper's N^2 indicator sum becomes N log N work per lambda.
+#include "internal.h"
+#include "ybar.cuh"
+
+namespace ppabc {
+
+namespace {
+
+constexpr int kWiThreads = 1024;
+constexpr int kWiMaxPerThread = PPABC_WEAKINF_MAX_SETS / kWiThreads;
+
+__global__ void __launch_bounds__(kWiThreads) weakinf_kernel(
+    const double* __restrict__ lambda, double lambda0, uint32_t n_obs, double inv_n, uint32_t N,
+    uint32_t P /* power of two >= N */, uint32_t rank /* ceil(alpha N), 1-based */,
+    const __grid_constant__ PhiloxKeys K, double* __restrict__ gamma_out,
+    uint32_t* __restrict__ counts_out) {
+  extern __shared__ double smem[];  // P doubles; later reused as N+1 histogram bins
+  __shared__ unsigned int scan_smem[kWiThreads / 32];
+  __shared__ unsigned int s_answer;
+  const uint32_t k = blockIdx.x;
+  const double lam = lambda[k];
+  // 1. |ybar| of the lambda_k data sets, padded with +inf to P entries.
+  for (uint32_t j = threadIdx.x; j < P; j += kWiThreads)
+    smem[j] = j < N ? fabs(dataset_ybar(K, lam, n_obs, inv_n, j, k, kTagPath)) : __longlong_as_double(0x7FF0000000000000ll);
+  __syncthreads();
+  // 2. Bitonic sort, ascending.
+  for (uint32_t size = 2; size <= P; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t t = threadIdx.x; t < (P >> 1); t += kWiThreads) {
+        const uint32_t lo = 2 * t - (t & (stride - 1));
+        const uint32_t hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const double a = smem[lo], b = smem[hi];
+        if ((a > b) == up) {
+          smem[lo] = b;
+          smem[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // 3. Counts of the base data sets: N - (first index with value >= |ybar_0|).
+  uint32_t my_counts[kWiMaxPerThread];
+#pragma unroll
+  for (int q = 0; q < kWiMaxPerThread; ++q) {
+    const uint32_t i = threadIdx.x + q * kWiThreads;
+    my_counts[q] = 0;
+    if (i < N) {
+      const double b = fabs(dataset_ybar(K, lambda0, n_obs, inv_n, i, k, kTagBase));
+      uint32_t lo = 0, hi = N;  // search in [0, N)
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (smem[mid] < b)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      my_counts[q] = N - lo;
+      if (counts_out) counts_out[static_cast<size_t>(k) * N + i] = N - lo;
+    }
+  }
+  __syncthreads();
+  // 4. Histogram of the counts (values 0..N) in the same shared memory.
+  unsigned int* hist = reinterpret_cast<unsigned int*>(smem);
+  for (uint32_t v = threadIdx.x; v <= N; v += kWiThreads) hist[v] = 0u;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kWiMaxPerThread; ++q) {
+    const uint32_t i = threadIdx.x + q * kWiThreads;
+    if (i < N) atomicAdd(&hist[my_counts[q]], 1u);
+  }
+  __syncthreads();
+  // 5. The rank-th smallest count: each thread owns a contiguous run of bins.
+  const uint32_t bins = N + 1;
+  const uint32_t per = (bins + kWiThreads - 1) / kWiThreads;
+  const uint32_t v0 = threadIdx.x * per;
+  unsigned int mine = 0;
+  for (uint32_t v = v0; v < v0 + per && v < bins; ++v) mine += hist[v];
+  // block exclusive scan of `mine`
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned int x = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) scan_smem[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned int w = scan_smem[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+      if (lane >= o) w += y;
+    }
+    scan_smem[lane] = w;
+  }
+  __syncthreads();
+  const unsigned int before = (warp ? scan_smem[warp - 1] : 0u) + x - mine;
+  if (before < rank && rank <= before + mine) {
+    unsigned int run = before;
+    for (uint32_t v = v0; v < v0 + per && v < bins; ++v) {
+      run += hist[v];
+      if (run >= rank) {
+        s_answer = v;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) gamma_out[k] = static_cast<double>(s_answer) / static_cast<double>(N);
+}
+
+}  // namespace
+
+cudaError_t launch_weakinf(const double* lambda, uint32_t n_lambda, double lambda0, uint32_t n_obs,
+                           uint32_t n_sets, double alpha, uint64_t seed, double* gamma_out,
+                           uint32_t* counts_out, cudaStream_t s) {
+  uint32_t P = 1;
+  while (P < n_sets) P <<= 1;
+  if (P < 2) P = 2;
+  const size_t smem = sizeof(double) * (P > n_sets + 1 ? P : n_sets + 1);
+  cudaError_t e = cudaFuncSetAttribute(weakinf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  uint64_t rank = static_cast<uint64_t>(ceil(alpha * static_cast<double>(n_sets)));
+  if (rank < 1) rank = 1;
+  if (rank > n_sets) rank = n_sets;
+  weakinf_kernel<<<n_lambda, kWiThreads, smem, s>>>(lambda, lambda0, n_obs, 1.0 / static_cast<double>(n_obs),
+                                                    n_sets, P, static_cast<uint32_t>(rank),
+                                                    philox_keys(seed), gamma_out, counts_out);
+  return cudaGetLastError();
+}
+
+}  // namespace ppabc

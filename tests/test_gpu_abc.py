@@ -122,6 +122,9 @@ def _select_cases():
     yield "one", np.array([0.5])
     yield "specials", np.array([np.nan, 0.0, -0.0, np.inf, 1.0, 0.0, np.nan, 2.0, np.inf, 1e-300])
     yield "large", rng.exponential(size=1 << 21)
+    # around the single-CTA / multi-kernel boundary (4096 distances)
+    for n in (4095, 4096, 4097, 2049):
+        yield f"edge{n}", np.round(rng.exponential(size=n), 2)
 
 
 @pytest.mark.parametrize("case", [c for c, _ in _select_cases()])

@@ -68,3 +68,34 @@ def test_invalid_arguments():
         binding.pvalue_sweep(lt, 0, 10, 1.0, 1)
     with pytest.raises(binding.PPABCError):
         binding.pvalue_sweep(lt, 10, 0, 1.0, 1)
+
+
+# ---------------------------------------------------------------------------
+# Weak-informativity test (Algorithm 2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,n_obs", [(2000, 50), (4097, 7), (1, 3), (16384, 50)])
+def test_weakinf_matches_oracle(N, n_obs):
+    binding = require_gpu()
+    lams = np.array([0.05, 0.5, 1.0, 2.0, 10.0, 100.0])
+    lam0, alpha = 1.0, 0.05
+    out = binding.weakinf_test(torch.from_numpy(lams).cuda(), lam0, n_obs, N, alpha, seed=9,
+                               want_counts=True)
+    torch.cuda.synchronize()
+    g_o, c_o = oracle.weakinf(lams, lam0, n_obs, N, alpha, seed=9, want_counts=True)
+    c_g = to_np(out["counts"]).astype(np.int64)
+    diff = np.abs(c_g - c_o.astype(np.int64))
+    # a count differs only where binary32 normals move |ybar| across a near-tie
+    print(f"N={N}: counts equal for {np.mean(diff == 0):.6f} of base sets, max diff {diff.max()}")
+    assert diff.max() <= 2
+    assert np.mean(diff == 0) >= 0.999
+    assert np.all(np.abs(to_np(out["gamma"]) - g_o) <= 2.0 / N)
+
+
+def test_weakinf_invalid():
+    binding = require_gpu()
+    lt = torch.ones(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.PPABCError):
+        binding.weakinf_test(lt, 1.0, 50, binding.WEAKINF_MAX_SETS + 1, 0.05, 1)
+    with pytest.raises(binding.PPABCError):
+        binding.weakinf_test(lt, 1.0, 50, 100, 0.0, 1)
