@@ -385,6 +385,49 @@ int pvalue_sweep(const double *lambda, uint32_t n_lambda, uint32_t n_obs,
                  uint64_t *counts, double *p_out, double *ybar_out,
                  void *stream);
 
+/* Genetic toggle switch (the paper's example model). */
+#define PPABC_TOGGLE_NQ 19        /* summaries: quantiles at 0.05, 0.10, .., 0.95 */
+#define PPABC_TOGGLE_MAX_CELLS 16384
+#define PPABC_TAG_TOGGLE_PRIOR 4u
+#define PPABC_TAG_TOGGLE_PATH 5u
+
+/*
+ * Toggle-switch model (Sec. 3.2, Eq. 3-4): theta = (mu, sigma, gamma,
+ * alpha_u, alpha_v, beta_u, beta_v) with independent uniform priors
+ * U(lo[j], hi[j]) (the paper's box is U(250,400) x U(0.05,0.5) x
+ * U(0.05,0.35) x U(0,50)^2 x U(0,7)^2); C cells, T time points (T-1
+ * Euler-Maruyama steps of size 1, Eq. 5).
+ */
+typedef struct ppabc_toggle_model {
+  double lo[7];
+  double hi[7];
+  uint32_t T;  /* >= 2 */
+  uint32_t C;  /* 1 .. PPABC_TOGGLE_MAX_CELLS */
+} ppabc_toggle_model;
+
+/*
+ * Toggle-switch prior predictive for ABC, one sample per global index
+ * g = sample_base + i: theta from blocks (0|1, g, substream, TOGGLE_PRIOR);
+ * cell c evolves from u = v = 10 with, at step j = 1..T-1,
+ *   u = max(0.97 u + alpha_u / (1 + v^beta_u) - 1 + 0.5 zeta_u, 1),
+ *   v = max(0.97 v + alpha_v / (1 + u^beta_v) - 1 + 0.5 zeta_v, 1)
+ * (both from the previous u, v; zeta_u, zeta_v are normals 2(j-1), 2(j-1)+1
+ * of stream (g, c, (substream << 8) | TOGGLE_PATH)), and is observed as
+ * y = max(u + mu + mu sigma eta / u^gamma, 1), eta = normal 2(T-1).
+ * S(D*) = the quantiles at levels k/20, k = 1..19 (linear interpolation
+ * between order statistics: h = (C-1) k / 20), rho = ||S - q_obs||_2.
+ * The path is binary32; quantiles and rho are binary64.
+ *   h_q_obs     19 observed quantiles (host).
+ *   theta_out   nullable [7][n] float;  summ_out nullable [19][n] double;
+ *   y_out       nullable [n][C] float (every cell's observation);
+ *   dist_out    [n] double.
+ * Requires substream < 2^24 and sample_base + n <= 2^32.
+ */
+int toggle_prior_predictive(const ppabc_toggle_model *h_model, const double *h_q_obs,
+                            uint64_t n, uint64_t sample_base, uint64_t seed,
+                            uint32_t substream, float *theta_out, double *summ_out,
+                            float *y_out, double *dist_out, void *stream);
+
 /* Most data sets per hyperparameter in weakinf_test. */
 #define PPABC_WEAKINF_MAX_SETS 16384
 

@@ -39,7 +39,7 @@ EXPORTED = ("ppabc_abi_version", "ppabc_last_error", "ppabc_device_check", "ppab
             "ppabc_batch_plan_destroy", "ppabc_batch_run", "ppabc_server_create",
             "ppabc_server_submit", "ppabc_server_poll", "ppabc_server_wait", "ppabc_server_fetch",
             "ppabc_server_release", "ppabc_server_cancel", "ppabc_server_get_stats",
-            "ppabc_server_now", "ppabc_server_destroy", "weakinf_test")
+            "ppabc_server_now", "ppabc_server_destroy", "weakinf_test", "toggle_prior_predictive")
 WEAKINF_MAX_SETS = 16384
 PPABC_PENDING = 1
 JOB_ABC = 0
@@ -80,6 +80,20 @@ class ABCJob(ctypes.Structure):
                 ("rec_out", ctypes.c_void_p), ("cap", ctypes.c_uint64),
                 ("n_acc_out", ctypes.c_void_p), ("eps_out", ctypes.c_void_p),
                 ("post_out", ctypes.c_void_p)]
+
+
+class ToggleModel(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 7), ("hi", ctypes.c_double * 7),
+                ("T", ctypes.c_uint32), ("C", ctypes.c_uint32)]
+
+    @classmethod
+    def from_dict(cls, m: dict) -> "ToggleModel":
+        o = cls()
+        for j in range(7):
+            o.lo[j] = float(m["lo"][j])
+            o.hi[j] = float(m["hi"][j])
+        o.T, o.C = int(m["T"]), int(m["C"])
+        return o
 
 
 class TileConfig(ctypes.Structure):
@@ -165,6 +179,8 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
             "ppabc_server_now": ([P], dbl),
             "ppabc_server_destroy": ([P], i32),
             "weakinf_test": ([P, u32, dbl, u32, u64, dbl, u64, P, P, P], i32),
+            "toggle_prior_predictive": ([ctypes.POINTER(ToggleModel), P, u64, u64, u64, u32, P, P,
+                                         P, P, P], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -359,6 +375,25 @@ def weakinf_test(lambdas: torch.Tensor, lambda0: float, n_obs: int, n_sets: int,
                                        float(alpha), seed, _ptr(gamma), _ptr(counts),
                                        _stream(stream)))
     return {"gamma": gamma, "counts": counts}
+
+
+def toggle_prior_predictive(model: dict, q_obs, n: int, seed: int, substream: int = 0,
+                            sample_base: int = 0, want_theta: bool = False, want_summ: bool = False,
+                            want_y: bool = False, stream=None) -> dict:
+    """Toggle-switch prior predictive: {"theta": [7,n] f32, "summ": [19,n] f64,
+    "y": [n,C] f32, "dist": [n] f64} (unrequested outputs are None)."""
+    m = ToggleModel.from_dict(model)
+    dev = torch.device("cuda")
+    q = (ctypes.c_double * 19)(*[float(v) for v in (q_obs.tolist() if hasattr(q_obs, "tolist")
+                                                    else q_obs)])
+    dist = torch.empty(n, dtype=torch.float64, device=dev)
+    theta = torch.empty((7, n), dtype=torch.float32, device=dev) if want_theta else None
+    summ = torch.empty((19, n), dtype=torch.float64, device=dev) if want_summ else None
+    y = torch.empty((n, m.C), dtype=torch.float32, device=dev) if want_y else None
+    _check(load_library().toggle_prior_predictive(ctypes.byref(m), q, n, sample_base, seed, substream,
+                                                  _ptr(theta), _ptr(summ), _ptr(y), _ptr(dist),
+                                                  _stream(stream)))
+    return {"theta": theta, "summ": summ, "y": y, "dist": dist}
 
 
 # ---------------------------------------------------------------------------

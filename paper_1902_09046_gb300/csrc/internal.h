@@ -43,6 +43,20 @@ cudaError_t launch_pvalue(const double* lambda, uint32_t n_lambda, uint32_t n_ob
                           uint64_t* counts,
                           double* p_out, double* ybar_out, cudaStream_t s);
 
+// Toggle switch: launch constants (binary32 prior box, sizes, observed
+// quantiles, Philox key).
+struct ToggleConst {
+  float lo[7];
+  float span[7];
+  uint32_t T;
+  uint32_t C;
+  uint32_t sub;
+  PhiloxKeys keys;
+  double q_obs[PPABC_TOGGLE_NQ];
+};
+cudaError_t launch_toggle(const ToggleConst& P, uint64_t base, uint32_t n, float* theta_out,
+                          double* summ_out, float* y_out, double* dist_out, cudaStream_t s);
+
 // Weak-informativity test.
 cudaError_t launch_weakinf(const double* lambda, uint32_t n_lambda, double lambda0, uint32_t n_obs,
                            uint32_t n_sets, double alpha, uint64_t seed, double* gamma_out,

@@ -240,4 +240,44 @@ int weakinf_test(const double* lambda, uint32_t n_lambda, double lambda0, uint32
                     "weakinf launch");
 }
 
+int toggle_prior_predictive(const ppabc_toggle_model* h_model, const double* h_q_obs, uint64_t n,
+                            uint64_t sample_base, uint64_t seed, uint32_t substream, float* theta_out,
+                            double* summ_out, float* y_out, double* dist_out, void* stream) {
+  if (!h_model || !h_q_obs) return set_error(PPABC_EINVAL, "h_model and h_q_obs must be non-NULL");
+  if (h_model->T < 2) return set_error(PPABC_EINVAL, "T must be >= 2");
+  if (h_model->C < 1 || h_model->C > PPABC_TOGGLE_MAX_CELLS)
+    return set_error(PPABC_EINVAL, "C must be in [1, %d]", PPABC_TOGGLE_MAX_CELLS);
+  for (int j = 0; j < 7; ++j)
+    if (!isfinite(h_model->lo[j]) || !isfinite(h_model->hi[j]) || h_model->lo[j] > h_model->hi[j])
+      return set_error(PPABC_EINVAL, "prior bound %d must be finite with lo <= hi", j);
+  if (h_model->lo[0] < 0.0 || h_model->lo[1] < 0.0 || h_model->lo[2] < 0.0 || h_model->lo[5] < 0.0 ||
+      h_model->lo[6] < 0.0)
+    return set_error(PPABC_EINVAL, "mu, sigma, gamma and beta must have non-negative priors");
+  if (substream >= (1u << 24)) return set_error(PPABC_EINVAL, "substream must be < 2^24");
+  if (sample_base > 0x100000000ull || n > 0x100000000ull - sample_base)
+    return set_error(PPABC_EINVAL, "sample_base + n must be <= 2^32");
+  if (n == 0) return PPABC_OK;
+  if (n > 0x7FFFFFFFull) return set_error(PPABC_EINVAL, "n must be < 2^31");
+  if (!dist_out) return set_error(PPABC_EINVAL, "dist_out is NULL");
+  ToggleConst P;
+  memset(&P, 0, sizeof(P));
+  for (int j = 0; j < 7; ++j) {
+    P.lo[j] = static_cast<float>(h_model->lo[j]);
+    P.span[j] = static_cast<float>(h_model->hi[j] - h_model->lo[j]);
+  }
+  P.T = h_model->T;
+  P.C = h_model->C;
+  P.sub = substream;
+  P.keys = philox_keys(seed);
+  for (int k = 0; k < PPABC_TOGGLE_NQ; ++k) {
+    if (!isfinite(h_q_obs[k])) return set_error(PPABC_EINVAL, "q_obs[%d] is not finite", k);
+    P.q_obs[k] = h_q_obs[k];
+  }
+  int rc = require_device();
+  if (rc) return rc;
+  return check_cuda(launch_toggle(P, sample_base, static_cast<uint32_t>(n), theta_out, summ_out, y_out,
+                                  dist_out, static_cast<cudaStream_t>(stream)),
+                    "toggle launch");
+}
+
 }  // extern "C"
