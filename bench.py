@@ -50,7 +50,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--mode", choices=("path", "batch", "serve"), default="path",
+    ap.add_argument("--mode", choices=("path", "batch", "serve", "toggle"), default="path",
                     help="path: the headline step; batch: 256 uneven jobs, plain vs persistent; "
                          "serve: Poisson arrivals, served vs plain")
     ap.add_argument("--jobs", type=int, default=256)
@@ -245,6 +245,23 @@ def profiled_traffic(n_samples):
     return float(rec["dram_bytes"]) * n_samples / float(rec["n_samples"])
 
 
+def issue_bound(ms_per_launch, path_steps):
+    """The instruction-issue ceiling of the kernel from its measured
+    instructions per path-step (committed ncu summary), None if absent."""
+    path = os.path.join(ROOT, "profiles", "em_ou_fused_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ipp = rec.get("instructions_per_path_step")
+    if not ipp or rec.get("source_hash") != kernel_source_hash():
+        return None
+    ceiling = SM_COUNT * 128 * SM_MAX_MHZ * 1e6 / ipp
+    achieved = path_steps / (ms_per_launch / 1e3)
+    return {"instructions_per_path_step": ipp, "ceiling_path_steps_per_s": ceiling,
+            "frac": achieved / ceiling}
+
+
 def gpu_arm(args):
     import torch
     from paper_1902_09046_gb300 import binding
@@ -363,11 +380,12 @@ def gpu_arm(args):
     em_avg_s = statistics.mean(em_ms) / 1e3
     achieved = abc_steps / em_avg_s / 1e9
     peak = SM_COUNT * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / MUFU_PER_PATH_STEP / 1e9
-    roof = {"kernel": "em_ou_fused", "bound": "alu", "achieved": achieved, "peak": peak,
+    roof = {"kernel": "em_ou_fused_x2", "bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "Gpath-steps/s", "frac": achieved / peak, "traffic": profiled_traffic(N),
             "peak_basis": "FP32+MUFU roofline: 2 MUFU ops/path-step (log,sqrt,sin,cos per pair), "
                           "16 MUFU/SM/clk x 152 SMs x 2070 MHz; FP32 pipe bound (6 ops/step, "
-                          "128/SM/clk) is looser"}
+                          "128/SM/clk) is looser",
+            "issue_bound": issue_bound(statistics.mean(em_ms), abc_steps)}
     clock = clocks.summary()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
@@ -537,6 +555,59 @@ def serve_mode(args):
     return 0
 
 
+PAPER_TOGGLE_SECONDS = 69.0  # N=8064, T=600, C=8000 on a Xeon Gold 6140 (AVX-512, P=16)
+
+
+def toggle_mode(args):
+    """The paper's benchmark: N = 8064 toggle-switch prior-predictive samples,
+    T = 600 time points, C = 8000 cells, with the 19-quantile summaries and the
+    distance to an observed target; cell-steps per second."""
+    import torch
+    from paper_1902_09046_gb300 import binding
+    from paper_1902_09046_gb300 import build as libbuild
+
+    torch.cuda.set_device(0)
+    libbuild.build()
+    binding.device_check()
+    N, model = 8064, workloads.toggle_model()
+    q = workloads.toggle_observed_quantiles()
+    cell_steps = N * model["C"] * (model["T"] - 1)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        binding.toggle_prior_predictive(model, q, N, 1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(0) as clocks:
+        for a, b in ev:
+            a.record(stream)
+            binding.toggle_prior_predictive(model, q, N, 1)
+            b.record(stream)
+        torch.cuda.synchronize()
+    ms = statistics.median([a.elapsed_time(b) for a, b in ev])
+    line = {"mode": "toggle", "metric": "toggle-switch prior-predictive cell-steps/s",
+            "unit": "cell-steps/s", "value": cell_steps / (ms / 1e3), "ms_per_run": ms,
+            "higher_is_better": True, "vs_baseline": (PAPER_TOGGLE_SECONDS * 1e3) / ms,
+            "baseline": "paper Table A.1: 69 s for this workload, C with AVX-512, 16 cores",
+            "dtype": "f32", "data": "synthetic (seeded)", "steps": args.steps,
+            "config": {"workload": "toggle switch N=8064 T=600 C=8000, 19 quantiles + distance"},
+            "clocks": clocks.summary()}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        thr = oracle.default_threads()
+        n_cpu = 2 * thr
+        t0 = time.perf_counter()
+        oracle.toggle_prior_predictive(model, q, n_cpu, 1, want_theta=False, want_summ=False,
+                                       n_threads=thr)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": n_cpu * model["C"] * (model["T"] - 1) / dt,
+                                "unit": "cell-steps/s", "cores": thr, "kind": "oracle",
+                                "sample": f"{n_cpu} of the 8064 samples, FP64, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -545,6 +616,8 @@ def main():
         return batch_mode(args)
     if args.mode == "serve":
         return serve_mode(args)
+    if args.mode == "toggle":
+        return toggle_mode(args)
     return gpu_arm(args)
 
 

@@ -6,11 +6,22 @@
 // This replaces the paper's block-of-VECL SIMD loop with pre-generated
 // normals (Sec. 3.4): on the GPU a warp is the SIMD vector, the sample index
 // is the lane, and the normals never touch memory.
+#include <stdlib.h>
+
 #include "internal.h"
 
 namespace ppabc {
 
 constexpr int kEmThreads = 128;
+
+// PPABC_EM_PAIRS=0 selects the one-sample-per-thread kernel (for comparison).
+bool em_pairs_enabled() {
+  static const bool on = [] {
+    const char* v = getenv("PPABC_EM_PAIRS");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
 
 template <bool kWantTheta, bool kWantSumm>
 __global__ void __launch_bounds__(kEmThreads) em_ou_fused(const __grid_constant__ OUConst P,
@@ -31,9 +42,33 @@ __global__ void __launch_bounds__(kEmThreads) em_ou_fused(const __grid_constant_
   dist_out[i] = ou_path<kWantSumm>(P, g, th1, th2, th3, kWantSumm ? summ_out + i : nullptr, n);
 }
 
+// Two samples per thread (samples i and i + half of each CTA's 2x128
+// range), interleaved; see ou_path2.  Used when neither theta nor the
+// summaries are requested (the benchmark and batch paths).
+__global__ void __launch_bounds__(kEmThreads) em_ou_fused_x2(const __grid_constant__ OUConst P,
+                                                             uint32_t base, uint32_t n,
+                                                             double* __restrict__ dist_out) {
+  const uint32_t i0 = blockIdx.x * (2 * kEmThreads) + threadIdx.x;
+  const uint32_t i1 = i0 + kEmThreads;
+  if (i0 >= n) return;
+  const uint32_t gi[2] = {base + i0, base + (i1 < n ? i1 : i0)};
+  float th1[2], th2[2], th3[2];
+  ou_prior(P, gi[0], th1[0], th2[0], th3[0]);
+  ou_prior(P, gi[1], th1[1], th2[1], th3[1]);
+  double d[2];
+  ou_path2<false>(P, gi, th1, th2, th3, nullptr, nullptr, 0, d);
+  dist_out[i0] = d[0];
+  if (i1 < n) dist_out[i1] = d[1];
+}
+
 cudaError_t launch_em_ou(const OUConst& P, uint64_t base, uint32_t n, float* theta_out,
                          double* summ_out, double* dist_out, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
+  if (!theta_out && !summ_out && em_pairs_enabled()) {
+    const dim3 grid2((n + 2 * kEmThreads - 1) / (2 * kEmThreads));
+    em_ou_fused_x2<<<grid2, kEmThreads, 0, s>>>(P, static_cast<uint32_t>(base), n, dist_out);
+    return cudaGetLastError();
+  }
   const dim3 grid((n + kEmThreads - 1) / kEmThreads);
   const uint32_t b = static_cast<uint32_t>(base);
   if (theta_out && summ_out)

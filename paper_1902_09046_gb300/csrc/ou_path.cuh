@@ -121,4 +121,77 @@ __device__ __forceinline__ double ou_path(const OUConst& P, uint32_t g, float th
   return sqrt(acc);
 }
 
+// Two samples per thread, interleaved step by step: the same arithmetic as
+// ou_path on each sample (bit-identical results), with two independent
+// dependency chains so a warp has work for the FP32 pipes while the other
+// chain's Philox wide multiplies occupy the integer multiplier.  Both samples
+// share the launch's step count and observation steps, so the control flow
+// is the same as for one sample.
+template <bool kWantSumm>
+__device__ __forceinline__ void ou_path2(const OUConst& P, const uint32_t g[2], const float th1[2],
+                                         const float th2[2], const float th3[2], double* summ0,
+                                         double* summ1, uint32_t summ_stride, double out[2]) {
+  float k[2], c[2], Y[2], comp[2];
+  double th2d[2], acc[2];
+  PhiloxStream stream[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    k[q] = th1[q] * P.dt;
+    c[q] = th3[q] * P.sqrt_dt;
+    Y[q] = P.x0 - th2[q];
+    const float bb = Y[q] - P.x0;
+    const float err = (P.x0 - (Y[q] - bb)) + (-th2[q] - bb);
+    comp[q] = -err;
+    th2d[q] = static_cast<double>(th2[q]);
+    acc[q] = 0.0;
+    stream[q] = philox_stream(P.keys, g[q], P.sub, kTagPath);
+  }
+  const uint32_t S = P.n_steps;
+  const uint32_t n_obs = P.n_obs;
+  uint32_t s = 0, b = 0, j = 0;
+  while (j < n_obs) {
+    uint32_t s_next = P.s_obs[j];
+    const uint32_t b_end = b + (s_next > s + 4u ? (s_next - s - 1u) >> 2 : 0u);
+    s += (b_end - b) << 2;
+    for (; b < b_end; ++b) {
+      const float4 z0 = scaled_normals_of(philox_block(stream[0], P.keys, b), c[0]);
+      const float4 z1 = scaled_normals_of(philox_block(stream[1], P.keys, b), c[1]);
+      em_step(Y[0], comp[0], k[0], z0.x);
+      em_step(Y[1], comp[1], k[1], z1.x);
+      em_step(Y[0], comp[0], k[0], z0.y);
+      em_step(Y[1], comp[1], k[1], z1.y);
+      em_step(Y[0], comp[0], k[0], z0.z);
+      em_step(Y[1], comp[1], k[1], z1.z);
+      em_step(Y[0], comp[0], k[0], z0.w);
+      em_step(Y[1], comp[1], k[1], z1.w);
+    }
+    const float4 z0 = scaled_normals_of(philox_block(stream[0], P.keys, b), c[0]);
+    const float4 z1 = scaled_normals_of(philox_block(stream[1], P.keys, b), c[1]);
+    ++b;
+    const float zz0[4] = {z0.x, z0.y, z0.z, z0.w};
+    const float zz1[4] = {z1.x, z1.y, z1.z, z1.w};
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      if (s < S) {
+        em_step(Y[0], comp[0], k[0], zz0[l]);
+        em_step(Y[1], comp[1], k[1], zz1[l]);
+        ++s;
+        if (s == s_next) {
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const double x = th2d[q] + (static_cast<double>(Y[q]) - static_cast<double>(comp[q]));
+            const double r = x - P.y[j];
+            acc[q] = fma(r, r, acc[q]);
+            if (kWantSumm) (q ? summ1 : summ0)[static_cast<size_t>(j) * summ_stride] = x;
+          }
+          ++j;
+          s_next = (j < n_obs) ? P.s_obs[j] : 0xFFFFFFFFu;
+        }
+      }
+    }
+  }
+  out[0] = sqrt(acc[0]);
+  out[1] = sqrt(acc[1]);
+}
+
 }  // namespace ppabc

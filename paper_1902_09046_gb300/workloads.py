@@ -180,3 +180,28 @@ def served_jobs(rate_per_s: float = 200.0, duration_s: float = 60.0, abc_frac: f
         jobs.append(job)
         jid += 1
     return jobs
+
+
+# --------------------------------------------------------------------------
+# Genetic toggle switch (the paper's example model).
+# --------------------------------------------------------------------------
+
+TOGGLE_PRIOR_LO = (250.0, 0.05, 0.05, 0.0, 0.0, 0.0, 0.0)
+TOGGLE_PRIOR_HI = (400.0, 0.5, 0.35, 50.0, 50.0, 7.0, 7.0)
+
+
+def toggle_model(T: int = 600, C: int = 8000) -> dict:
+    """Prior box of the paper's toggle-switch example; T time points, C cells."""
+    return {"lo": TOGGLE_PRIOR_LO, "hi": TOGGLE_PRIOR_HI, "T": int(T), "C": int(C)}
+
+
+def toggle_observed_quantiles(seed: int = 7) -> np.ndarray:
+    """A synthetic target for the 19 summary quantiles: the quantiles at levels
+    0.05..0.95 of a right-skewed intensity distribution (shifted lognormal,
+    PCG64-drawn location and scale), standing in for observed cell data."""
+    rng = np.random.default_rng(seed)
+    loc = float(rng.uniform(300.0, 350.0))
+    scale = float(rng.uniform(0.3, 0.6))
+    from scipy import stats
+    levels = np.arange(1, 20) / 20.0
+    return loc + 100.0 * stats.lognorm.ppf(levels, s=scale)

@@ -95,6 +95,18 @@ def test_fixed_theta_and_sample_base_sharding():
     np.testing.assert_array_equal(to_np(full["theta"])[:, 4096:], to_np(half["theta"]))
 
 
+@pytest.mark.parametrize("n", [1, 255, 256, 257, 100_001])
+def test_two_paths_per_thread_is_bit_identical(n):
+    """Without theta or summary outputs the kernel runs two interleaved paths
+    per thread; every distance equals the one-path-per-thread kernel's."""
+    binding = require_gpu()
+    w = workloads.abc_small()
+    a = binding.abc_prior_predictive(w.model, w.y_obs, n, w.seed, sample_base=77, want_theta=False)
+    b = binding.abc_prior_predictive(w.model, w.y_obs, n, w.seed, sample_base=77, want_theta=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(to_np(a["dist"]), to_np(b["dist"]))
+
+
 def test_empty_and_invalid():
     binding = require_gpu()
     w = workloads.abc_small()
