@@ -50,7 +50,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--mode", choices=("path", "batch", "serve", "toggle"), default="path",
+    ap.add_argument("--mode", choices=("path", "batch", "serve", "toggle", "configs"), default="path",
                     help="path: the headline step; batch: 256 uneven jobs, plain vs persistent; "
                          "serve: Poisson arrivals, served vs plain")
     ap.add_argument("--jobs", type=int, default=256)
@@ -608,6 +608,67 @@ def toggle_mode(args):
     return 0
 
 
+def configs_mode(args):
+    """Each synthetic configuration timed on its own (GPU, CUDA events, median
+    of --steps after warm-up), with the oracle on a bounded sample of it."""
+    import torch
+    import oracle
+    from paper_1902_09046_gb300 import binding
+    from paper_1902_09046_gb300 import build as libbuild
+
+    torch.cuda.set_device(0)
+    libbuild.build()
+    oracle.build()
+    binding.device_check()
+    thr = oracle.default_threads()
+    stream = torch.cuda.current_stream()
+
+    def gpu_ms(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return statistics.median([a.elapsed_time(b) for a, b in ev])
+
+    rows = []
+    for name, w in (("ou_abc_n1e4_s1e3", workloads.abc_small()), ("ou_abc_n2p24_s1e4", workloads.abc_large())):
+        ws = torch.empty(binding.abc_select_workspace_bytes(w.n_samples), dtype=torch.uint8, device="cuda")
+        dist = torch.empty(w.n_samples, dtype=torch.float64, device="cuda")
+
+        def run(w=w, ws=ws, dist=dist):
+            binding.abc_prior_predictive(w.model, w.y_obs, w.n_samples, w.seed, want_theta=False,
+                                         out={"dist": dist})
+            binding.abc_select(dist, k=w.k_accept, model=w.model, seed=w.seed, workspace=ws)
+        ms = gpu_ms(run)
+        steps = w.n_samples * w.model["n_steps"]
+        n_cpu = min(w.n_samples, max(thr * 16, int(2e8 / w.model["n_steps"])))
+        t0 = time.perf_counter()
+        oracle.ou_prior_predictive(w.model, w.y_obs, n_cpu, w.seed, want_theta=False, n_threads=thr)
+        cpu_s = time.perf_counter() - t0
+        rows.append({"config": name, "gpu_ms": ms, "gpu_path_steps_per_s": steps / (ms / 1e3),
+                     "oracle_path_steps_per_s": n_cpu * w.model["n_steps"] / cpu_s,
+                     "oracle_sample": f"{n_cpu} samples", "oracle_cores": thr})
+    pv = workloads.pvalue_sweep_workload()
+    lam = torch.from_numpy(pv.lambdas).cuda()
+    ms = gpu_ms(lambda: binding.pvalue_sweep(lam, pv.n_obs, pv.m_sets, pv.ybar_obs, pv.seed))
+    steps = len(pv.lambdas) * pv.m_sets * (pv.n_obs + 1)
+    m_cpu = 20_000
+    t0 = time.perf_counter()
+    oracle.pvalue_sweep(pv.lambdas, pv.n_obs, m_cpu, pv.ybar_obs, pv.seed, n_threads=thr)
+    cpu_s = time.perf_counter() - t0
+    rows.append({"config": "pvalue_k64_n50_m1e6", "gpu_ms": ms, "gpu_path_steps_per_s": steps / (ms / 1e3),
+                 "oracle_path_steps_per_s": len(pv.lambdas) * m_cpu * (pv.n_obs + 1) / cpu_s,
+                 "oracle_sample": f"M={m_cpu} per lambda", "oracle_cores": thr})
+    print(json.dumps({"mode": "configs", "unit": UNIT, "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -618,6 +679,8 @@ def main():
         return serve_mode(args)
     if args.mode == "toggle":
         return toggle_mode(args)
+    if args.mode == "configs":
+        return configs_mode(args)
     return gpu_arm(args)
 
 

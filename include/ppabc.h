@@ -179,6 +179,31 @@ int abc_select(const double *dist, uint64_t n, uint64_t k, double eps,
                uint64_t *n_acc_out, double *eps_out, double *post_out,
                void *workspace, size_t workspace_bytes, void *stream);
 
+/* Bytes of scratch abc_rejection needs for a chunk size (256-byte aligned). */
+size_t abc_rejection_workspace_bytes(uint64_t chunk);
+
+/*
+ * ABC rejection as Algorithm 1 states it: proposals g = 0, 1, 2, ... are
+ * simulated as in abc_prior_predictive and accepted when rho <= eps, until
+ * m_accept samples are accepted or max_samples proposals are spent.
+ * Proposals are taken in index order, so the accepted set is the first
+ * m_accept samples of the sequence with rho <= eps, independent of `chunk`
+ * (the proposals simulated per launch).
+ *   idx_out   [m_accept] uint32 global sample indices, ascending;
+ *   rec_out   [m_accept][4] float (th1, th2, th3, (float)rho), 16-byte aligned;
+ *   h_counts  host [2]: accepted (<= m_accept), proposals used -- the index
+ *             of the m_accept-th acceptance + 1, or every proposal simulated
+ *             if fewer were accepted (m_accept / h_counts[1] estimates the
+ *             acceptance probability).
+ * The host checks the count every 4 chunks, so this call synchronises
+ * `stream`; up to 3 chunks past the last acceptance may be simulated (their
+ * results are not used).  workspace: abc_rejection_workspace_bytes(chunk).
+ */
+int abc_rejection(const ppabc_ou_model *h_model, const double *h_y_obs, double eps,
+                  uint64_t m_accept, uint64_t max_samples, uint64_t chunk, uint64_t seed,
+                  uint32_t substream, uint32_t *idx_out, float *rec_out, uint64_t *h_counts,
+                  void *workspace, size_t workspace_bytes, void *stream);
+
 /* Largest n that abc_select_static accepts. */
 #define PPABC_STATIC_SELECT_MAX_N (1ull << 24)
 

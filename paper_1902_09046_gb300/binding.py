@@ -39,7 +39,8 @@ EXPORTED = ("ppabc_abi_version", "ppabc_last_error", "ppabc_device_check", "ppab
             "ppabc_batch_plan_destroy", "ppabc_batch_run", "ppabc_server_create",
             "ppabc_server_submit", "ppabc_server_poll", "ppabc_server_wait", "ppabc_server_fetch",
             "ppabc_server_release", "ppabc_server_cancel", "ppabc_server_get_stats",
-            "ppabc_server_now", "ppabc_server_destroy", "weakinf_test", "toggle_prior_predictive")
+            "ppabc_server_now", "ppabc_server_destroy", "weakinf_test", "toggle_prior_predictive",
+            "abc_rejection_workspace_bytes", "abc_rejection")
 WEAKINF_MAX_SETS = 16384
 PPABC_PENDING = 1
 JOB_ABC = 0
@@ -179,6 +180,8 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
             "ppabc_server_now": ([P], dbl),
             "ppabc_server_destroy": ([P], i32),
             "weakinf_test": ([P, u32, dbl, u32, u64, dbl, u64, P, P, P], i32),
+            "abc_rejection_workspace_bytes": ([u64], sz),
+            "abc_rejection": ([M, P, dbl, u64, u64, u64, u64, u32, P, P, P, P, sz, P], i32),
             "toggle_prior_predictive": ([ctypes.POINTER(ToggleModel), P, u64, u64, u64, u32, P, P,
                                          P, P, P], i32),
         }
@@ -340,6 +343,25 @@ def abc_select_static(dist: torch.Tensor, k: int = 0, eps: float = math.inf,
     res["idx"] = res["idx"][:cap]
     res["rec"] = res["rec"][:cap]
     return res
+
+
+def abc_rejection(model: dict, y_obs, eps: float, m_accept: int, max_samples: int, seed: int,
+                  chunk: int = 1 << 20, substream: int = 0, stream=None) -> dict:
+    """Algorithm 1: the first m_accept proposals with rho <= eps.  Returns
+    {"idx": [n_acc] u32, "rec": [n_acc,4] f32, "n_acc": int, "tried": int}."""
+    m = OUModel.from_dict(model)
+    dev = torch.device("cuda")
+    idx = torch.empty(m_accept, dtype=torch.uint32, device=dev)
+    rec = torch.empty((m_accept, 4), dtype=torch.float32, device=dev)
+    lib = load_library()
+    ws_bytes = int(lib.abc_rejection_workspace_bytes(chunk))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    counts = (ctypes.c_uint64 * 2)()
+    _check(lib.abc_rejection(ctypes.byref(m), _y_obs_host(y_obs), float(eps), m_accept, max_samples,
+                             chunk, seed, substream, _ptr(idx), _ptr(rec), counts, _ptr(ws), ws_bytes,
+                             _stream(stream)))
+    n = int(counts[0])
+    return {"idx": idx[:n], "rec": rec[:n], "n_acc": n, "tried": int(counts[1])}
 
 
 def pvalue_sweep(lambdas: torch.Tensor, n_obs: int, m_sets: int, ybar_obs: float, seed: int,

@@ -247,3 +247,47 @@ def test_full_size_workload_sampled():
     rec = to_np(sel["rec"])
     th1 = rec[:, 0]
     assert np.all((th1 >= 0.1) & (th1 <= 2.0))
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 as stated: accept until M acceptances
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("chunk", [1000, 4096, 65_536])
+def test_rejection_until_m_accepted(chunk):
+    binding = require_gpu()
+    w = workloads.abc_small()
+    M = 200
+    # epsilon at the 2% point of the oracle's distances: about 10^4 proposals needed
+    _, _, d_o = oracle.ou_prior_predictive(w.model, w.y_obs, 30_000, seed=w.seed)
+    eps = float(np.quantile(d_o, 0.02))
+    res = binding.abc_rejection(w.model, w.y_obs, eps, M, 30_000, w.seed, chunk=chunk)
+    torch.cuda.synchronize()
+    assert res["n_acc"] == M
+    idx = to_np(res["idx"]).astype(np.int64)
+    assert np.all(np.diff(idx) > 0) and idx[-1] + 1 == res["tried"]
+    # the oracle's first M acceptances in index order, up to band members
+    acc_o = np.nonzero(d_o <= eps)[0]
+    ref = acc_o[:M]
+    diff = np.setxor1d(idx, ref)
+    assert all(abs(d_o[i] - eps) < 1e-6 * eps for i in diff), diff
+    assert abs(res["tried"] - (ref[-1] + 1)) <= (0 if diff.size == 0 else 30_000)
+    rec = to_np(res["rec"])
+    assert np.all(rec[:, 3] <= np.float32(eps) * (1 + 1e-6))
+
+
+def test_rejection_budget_and_chunking_invariance():
+    binding = require_gpu()
+    w = workloads.abc_small()
+    a = binding.abc_rejection(w.model, w.y_obs, 0.5, 10_000, 5_000, w.seed, chunk=777)
+    b = binding.abc_rejection(w.model, w.y_obs, 0.5, 10_000, 5_000, w.seed, chunk=5_000)
+    torch.cuda.synchronize()
+    assert a["n_acc"] == b["n_acc"] < 10_000 and a["tried"] == b["tried"] == 5_000
+    np.testing.assert_array_equal(to_np(a["idx"]), to_np(b["idx"]))
+    np.testing.assert_array_equal(to_np(a["rec"]), to_np(b["rec"]))
+    # the threshold form of abc_select on the same prefix gives the same set
+    out = binding.abc_prior_predictive(w.model, w.y_obs, 5_000, w.seed, want_theta=False)
+    sel = binding.abc_select(out["dist"], k=0, eps=0.5, model=w.model, seed=w.seed)
+    torch.cuda.synchronize()
+    n = int(to_np(sel["n_acc"])[0])
+    np.testing.assert_array_equal(to_np(sel["idx"])[:n], to_np(a["idx"]))
