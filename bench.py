@@ -585,7 +585,16 @@ def toggle_mode(args):
             b.record(stream)
         torch.cuda.synchronize()
     ms = statistics.median([a.elapsed_time(b) for a, b in ev])
+    # Roofline: per cell-step the method needs 2 normals (1 Box-Muller pair: log, sqrt, sin,
+    # cos = 4 MUFU-class operations) and 2 powers (log2 + exp2 each) and 2 divisions
+    # (reciprocal each): 10 MUFU-class operations at 16 per SM per clock.
+    peak = SM_COUNT * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 10.0 / 1e9
+    achieved = cell_steps / (ms / 1e3) / 1e9
     line = {"mode": "toggle", "metric": "toggle-switch prior-predictive cell-steps/s",
+            "roofline": {"kernel": "toggle_abc", "bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "Gcell-steps/s", "frac": achieved / peak,
+                         "peak_basis": "10 MUFU-class ops per cell-step (Box-Muller pair 4, two "
+                                       "powers 4, two divisions 2) at 16/SM/clk x 152 SMs x 2070 MHz"},
             "unit": "cell-steps/s", "value": cell_steps / (ms / 1e3), "ms_per_run": ms,
             "higher_is_better": True, "vs_baseline": (PAPER_TOGGLE_SECONDS * 1e3) / ms,
             "baseline": "paper Table A.1: 69 s for this workload, C with AVX-512, 16 cores",
@@ -665,6 +674,30 @@ def configs_mode(args):
     rows.append({"config": "pvalue_k64_n50_m1e6", "gpu_ms": ms, "gpu_path_steps_per_s": steps / (ms / 1e3),
                  "oracle_path_steps_per_s": len(pv.lambdas) * m_cpu * (pv.n_obs + 1) / cpu_s,
                  "oracle_sample": f"M={m_cpu} per lambda", "oracle_cores": thr})
+    # Algorithm 2 (weak-informativity cut-offs): 64 lambdas x 2 x 16384 data sets of n = 50
+    wl = torch.from_numpy(workloads.pvalue_lambdas()).cuda()
+    N2 = binding.WEAKINF_MAX_SETS
+    ms = gpu_ms(lambda: binding.weakinf_test(wl, 1.0, 50, N2, 0.05, 9))
+    steps = 64 * 2 * N2 * 51
+    t0 = time.perf_counter()
+    oracle.weakinf(workloads.pvalue_lambdas()[:8], 1.0, 50, 2048, 0.05, 9, n_threads=thr)
+    cpu_s = time.perf_counter() - t0
+    rows.append({"config": "weakinf_k64_n50_N16384", "gpu_ms": ms, "gpu_path_steps_per_s": steps / (ms / 1e3),
+                 "oracle_path_steps_per_s": 8 * 2 * 2048 * 51 / cpu_s,
+                 "oracle_sample": "8 lambdas, N=2048 (its N^2 comparisons included)", "oracle_cores": thr})
+    # Algorithm 1 as stated: the first 10^4 acceptances at ~1% acceptance (OU, 1000 steps)
+    w = workloads.abc_small()
+    _, _, d_o = oracle.ou_prior_predictive(w.model, w.y_obs, 20_000, w.seed, n_threads=thr)
+    eps = float(np.quantile(d_o, 0.01))
+    res = {}
+
+    def rej():
+        res.update(binding.abc_rejection(w.model, w.y_obs, eps, 10_000, 1 << 22, w.seed, chunk=1 << 18))
+    ms = gpu_ms(rej)
+    rows.append({"config": "abc_rejection_ou_s1e3_m1e4", "gpu_ms": ms,
+                 "gpu_path_steps_per_s": res["tried"] * w.model["n_steps"] / (ms / 1e3),
+                 "proposals": res["tried"], "accepted": res["n_acc"],
+                 "note": "wall time includes the host check of the count every 4 chunks"})
     print(json.dumps({"mode": "configs", "unit": UNIT, "rows": rows}), flush=True)
     return 0
 

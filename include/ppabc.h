@@ -204,6 +204,34 @@ int abc_rejection(const ppabc_ou_model *h_model, const double *h_y_obs, double e
                   uint32_t substream, uint32_t *idx_out, float *rec_out, uint64_t *h_counts,
                   void *workspace, size_t workspace_bytes, void *stream);
 
+/* Most accepted samples abc_recalibrate takes. */
+#define PPABC_RECAL_MAX_Q 32768
+
+/* Bytes of scratch abc_recalibrate needs for n stored pairs and k neighbours. */
+size_t abc_recalibrate_workspace_bytes(uint64_t n, uint64_t k);
+
+/*
+ * ABC recalibration of an accepted sample (Sec. 5, Discussion: every
+ * accepted theta* is recalibrated with a further ABC posterior built from
+ * all stored (theta*, D*) pairs, taking its own D* as the observation,
+ * through the univariate marginal distribution functions).  For accepted
+ * i < q with a = acc_idx[i]:
+ *   N_i  = the k pairs j nearest to summ[:, a] (Euclidean over the n_obs
+ *          summaries, binary64 with one fma per coordinate in order; ties to
+ *          the smaller index; a itself is one of them),
+ *   u_out[d][i] = #{j in N_i : theta[d][j] <= theta[d][a]} / k,
+ *   theta_rc_out[d][i] = the ceil(u q)-th smallest (at least the first) of
+ *          theta[d][acc_idx[0..q-1]] -- the u-quantile of the accepted
+ *          marginal, i.e. of the posterior given the real observation.
+ *   summ     [n_obs][n] double (as abc_prior_predictive's summ_out);
+ *   theta    [3][n] float;  acc_idx [q] uint32 (indices >= n give NaN);
+ *   u_out    [3][q] double; theta_rc_out [3][q] float.
+ * Cost O(q n n_obs); q <= PPABC_RECAL_MAX_Q, 1 <= k <= n.
+ */
+int abc_recalibrate(const double *summ, const float *theta, uint64_t n, uint32_t n_obs,
+                    const uint32_t *acc_idx, uint64_t q, uint64_t k, double *u_out,
+                    float *theta_rc_out, void *workspace, size_t workspace_bytes, void *stream);
+
 /* Largest n that abc_select_static accepts. */
 #define PPABC_STATIC_SELECT_MAX_N (1ull << 24)
 

@@ -89,6 +89,8 @@ def _load():
             lib.orc_toggle_prior_predictive.argtypes = [ctypes.POINTER(_ToggleModel), P, u64, u64,
                                                         u64, u32, P, P, P, P, P, i32]
             lib.orc_toggle_prior_predictive.restype = i32
+            lib.orc_recalibrate.argtypes = [P, P, u64, u32, P, u64, u64, P, P, i32]
+            lib.orc_recalibrate.restype = i32
             _lib = lib
     return _lib
 
@@ -234,3 +236,21 @@ def toggle_prior_predictive(model: dict, q_obs, n: int, seed: int, sub: int = 0,
     if want_uv:
         return theta, summ, y, dist, uv
     return theta, summ, y, dist
+
+
+def recalibrate(summ: np.ndarray, theta: np.ndarray, acc: np.ndarray, k: int,
+                n_threads: int | None = None):
+    """ABC recalibration: summ [n_obs, n] float64, theta [3, n] float32, acc [q]
+    accepted indices -> (u [3, q] float64, theta_rc [3, q] float32)."""
+    S = np.ascontiguousarray(summ, dtype=np.float64)
+    th = np.ascontiguousarray(theta, dtype=np.float32)
+    a = np.ascontiguousarray(acc, dtype=np.uint32)
+    n_obs, n = S.shape
+    q = a.shape[0]
+    u = np.zeros((3, q), dtype=np.float64)
+    rc_out = np.zeros((3, q), dtype=np.float32)
+    rc = _load().orc_recalibrate(_ptr(S), _ptr(th), n, n_obs, _ptr(a), q, k, _ptr(u), _ptr(rc_out),
+                                 n_threads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle rejected the recalibration arguments")
+    return u, rc_out

@@ -650,3 +650,111 @@ int orc_toggle_prior_predictive(const orc_toggle_model *m, const double *q_obs, 
   free(th);
   return rc;
 }
+
+/* ---------------------------------------------------------------------------
+ * ABC recalibration (Discussion, Sec. 5): every accepted theta* is recalibrated
+ * with a further ABC posterior built from all stored (theta, D) pairs, taking
+ * its own simulated data D* as the observation, through the univariate
+ * marginal posterior distribution functions: u = F(theta* | D*) from the k
+ * nearest pairs, and the recalibrated value is the u-quantile of the
+ * accepted sample's marginal (the posterior given the real observation).
+ * ------------------------------------------------------------------------- */
+static int cmp_float_asc(const void *a, const void *b) {
+  float x = *(const float *)a, y = *(const float *)b;
+  return (x > y) - (x < y);
+}
+
+typedef struct rc_job {
+  const double *summ;
+  const float *theta;
+  uint64_t n, q, k, lo, hi;
+  uint32_t n_obs;
+  const uint32_t *acc;
+  double *u;
+  int rc;
+} rc_job;
+
+static void *rc_worker(void *arg) {
+  rc_job *J = (rc_job *)arg;
+  dist_idx *a = (dist_idx *)malloc((size_t)J->n * sizeof(dist_idx));
+  if (!a) {
+    J->rc = -1;
+    return NULL;
+  }
+  for (uint64_t i = J->lo; i < J->hi; ++i) {
+    uint64_t qa = J->acc[i];
+    for (uint64_t j = 0; j < J->n; ++j) {
+      double acc = 0.0;
+      for (uint32_t m = 0; m < J->n_obs; ++m) {
+        double r = J->summ[(uint64_t)m * J->n + j] - J->summ[(uint64_t)m * J->n + qa];
+        acc = fma(r, r, acc);
+      }
+      a[j].d = sqrt(acc);
+      a[j].i = j;
+    }
+    qsort(a, (size_t)J->n, sizeof(dist_idx), cmp_dist_idx);
+    for (int d = 0; d < 3; ++d) {
+      float t0 = J->theta[(uint64_t)d * J->n + qa];
+      uint64_t c = 0;
+      for (uint64_t t = 0; t < J->k; ++t)
+        if (J->theta[(uint64_t)d * J->n + a[t].i] <= t0) ++c;
+      J->u[(uint64_t)d * J->q + i] = (double)c / (double)J->k;
+    }
+  }
+  free(a);
+  return NULL;
+}
+
+int orc_recalibrate(const double *summ, const float *theta, uint64_t n, uint32_t n_obs,
+                    const uint32_t *acc, uint64_t q, uint64_t k, double *u, float *theta_rc,
+                    int n_threads) {
+  if (!summ || !theta || !acc || !u || !theta_rc || n == 0 || q == 0 || k == 0 || k > n) return -1;
+  for (uint64_t i = 0; i < q; ++i)
+    if (acc[i] >= n) return -1;
+  if (n_threads < 1) n_threads = 1;
+  if ((uint64_t)n_threads > q) n_threads = (int)q;
+  rc_job *jobs = (rc_job *)calloc((size_t)n_threads, sizeof(rc_job));
+  pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+  float *sorted = (float *)malloc((size_t)q * sizeof(float));
+  if (!jobs || !th || !sorted) {
+    free(jobs);
+    free(th);
+    free(sorted);
+    return -1;
+  }
+  for (int t = 0; t < n_threads; ++t) {
+    rc_job *J = &jobs[t];
+    J->summ = summ;
+    J->theta = theta;
+    J->n = n;
+    J->q = q;
+    J->k = k;
+    J->n_obs = n_obs;
+    J->acc = acc;
+    J->u = u;
+    J->lo = q * (uint64_t)t / (uint64_t)n_threads;
+    J->hi = q * (uint64_t)(t + 1) / (uint64_t)n_threads;
+  }
+  for (int t = 1; t < n_threads; ++t) pthread_create(&th[t], NULL, rc_worker, &jobs[t]);
+  rc_worker(&jobs[0]);
+  int rc = jobs[0].rc;
+  for (int t = 1; t < n_threads; ++t) {
+    pthread_join(th[t], NULL);
+    if (jobs[t].rc) rc = jobs[t].rc;
+  }
+  for (int d = 0; d < 3 && rc == 0; ++d) {
+    for (uint64_t i = 0; i < q; ++i) sorted[i] = theta[(uint64_t)d * n + acc[i]];
+    qsort(sorted, (size_t)q, sizeof(float), cmp_float_asc);
+    for (uint64_t i = 0; i < q; ++i) {
+      double uu = u[(uint64_t)d * q + i];
+      uint64_t r = (uint64_t)ceil(uu * (double)q);
+      if (r < 1) r = 1;
+      if (r > q) r = q;
+      theta_rc[(uint64_t)d * q + i] = sorted[r - 1];
+    }
+  }
+  free(jobs);
+  free(th);
+  free(sorted);
+  return rc;
+}

@@ -40,7 +40,8 @@ EXPORTED = ("ppabc_abi_version", "ppabc_last_error", "ppabc_device_check", "ppab
             "ppabc_server_submit", "ppabc_server_poll", "ppabc_server_wait", "ppabc_server_fetch",
             "ppabc_server_release", "ppabc_server_cancel", "ppabc_server_get_stats",
             "ppabc_server_now", "ppabc_server_destroy", "weakinf_test", "toggle_prior_predictive",
-            "abc_rejection_workspace_bytes", "abc_rejection")
+            "abc_rejection_workspace_bytes", "abc_rejection", "abc_recalibrate_workspace_bytes",
+            "abc_recalibrate")
 WEAKINF_MAX_SETS = 16384
 PPABC_PENDING = 1
 JOB_ABC = 0
@@ -182,6 +183,8 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
             "weakinf_test": ([P, u32, dbl, u32, u64, dbl, u64, P, P, P], i32),
             "abc_rejection_workspace_bytes": ([u64], sz),
             "abc_rejection": ([M, P, dbl, u64, u64, u64, u64, u32, P, P, P, P, sz, P], i32),
+            "abc_recalibrate_workspace_bytes": ([u64, u64], sz),
+            "abc_recalibrate": ([P, P, u64, u32, P, u64, u64, P, P, P, sz, P], i32),
             "toggle_prior_predictive": ([ctypes.POINTER(ToggleModel), P, u64, u64, u64, u32, P, P,
                                          P, P, P], i32),
         }
@@ -362,6 +365,23 @@ def abc_rejection(model: dict, y_obs, eps: float, m_accept: int, max_samples: in
                              _stream(stream)))
     n = int(counts[0])
     return {"idx": idx[:n], "rec": rec[:n], "n_acc": n, "tried": int(counts[1])}
+
+
+def abc_recalibrate(summ: torch.Tensor, theta: torch.Tensor, acc_idx: torch.Tensor, k: int,
+                    stream=None) -> dict:
+    """summ [n_obs,n] f64, theta [3,n] f32, acc_idx [q] u32 (CUDA) ->
+    {"u": [3,q] f64, "theta_rc": [3,q] f32}."""
+    n_obs, n = summ.shape
+    q = acc_idx.shape[0]
+    dev = summ.device
+    u = torch.empty((3, q), dtype=torch.float64, device=dev)
+    rc = torch.empty((3, q), dtype=torch.float32, device=dev)
+    lib = load_library()
+    ws_bytes = int(lib.abc_recalibrate_workspace_bytes(n, k))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    _check(lib.abc_recalibrate(_ptr(summ), _ptr(theta), n, n_obs, _ptr(acc_idx), q, k, _ptr(u), _ptr(rc),
+                               _ptr(ws), ws_bytes, _stream(stream)))
+    return {"u": u, "theta_rc": rc}
 
 
 def pvalue_sweep(lambdas: torch.Tensor, n_obs: int, m_sets: int, ybar_obs: float, seed: int,

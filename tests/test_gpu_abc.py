@@ -291,3 +291,41 @@ def test_rejection_budget_and_chunking_invariance():
     torch.cuda.synchronize()
     n = int(to_np(sel["n_acc"])[0])
     np.testing.assert_array_equal(to_np(sel["idx"])[:n], to_np(a["idx"]))
+
+
+# ---------------------------------------------------------------------------
+# ABC recalibration
+# ---------------------------------------------------------------------------
+
+def test_recalibration_matches_oracle_on_the_same_pairs():
+    """Same stored pairs on both sides (the GPU's own theta and summaries):
+    neighbour sets, u and the recalibrated values are identical."""
+    binding = require_gpu()
+    w = workloads.abc_small()
+    out = binding.abc_prior_predictive(w.model, w.y_obs, w.n_samples, w.seed, want_theta=True,
+                                       want_summ=True)
+    sel = binding.abc_select(out["dist"], k=w.k_accept, theta=out["theta"])
+    for k in (1, 100, 731):
+        rc = binding.abc_recalibrate(out["summ"], out["theta"], sel["idx"], k)
+        torch.cuda.synchronize()
+        u_o, rc_o = oracle.recalibrate(to_np(out["summ"]), to_np(out["theta"]), to_np(sel["idx"]), k)
+        np.testing.assert_array_equal(to_np(rc["u"]), u_o)
+        np.testing.assert_array_equal(to_np(rc["theta_rc"]), rc_o)
+        if k == 1:
+            assert np.all(to_np(rc["u"]) == 1.0)
+
+
+def test_recalibration_end_to_end_against_oracle_pairs():
+    """GPU pairs against the oracle's own pairs: u agrees to within the few
+    neighbours that sit on the k-th distance band."""
+    binding = require_gpu()
+    w = workloads.abc_small()
+    n, kacc, knn = 4000, 40, 200
+    out = binding.abc_prior_predictive(w.model, w.y_obs, n, w.seed, want_theta=True, want_summ=True)
+    sel = binding.abc_select(out["dist"], k=kacc, theta=out["theta"])
+    rc = binding.abc_recalibrate(out["summ"], out["theta"], sel["idx"], knn)
+    torch.cuda.synchronize()
+    th_o, s_o, d_o = oracle.ou_prior_predictive(w.model, w.y_obs, n, w.seed, want_summ=True)
+    acc = to_np(sel["idx"]).astype(np.uint32)
+    u_o, _ = oracle.recalibrate(s_o.T.copy(), th_o.T.astype(np.float32).copy(), acc, knn)
+    assert np.abs(to_np(rc["u"]) - u_o).max() <= 3.0 / knn
