@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kEmThreads) em_ou_fused(const __grid_constant_
 // Two samples per thread (samples i and i + half of each CTA's 2x128
 // range), interleaved; see ou_path2.  Used when neither theta nor the
 // summaries are requested (the benchmark and batch paths).
-__global__ void __launch_bounds__(kEmThreads) em_ou_fused_x2(const __grid_constant__ OUConst P,
+__global__ void __launch_bounds__(kEmThreads, 10) em_ou_fused_x2(const __grid_constant__ OUConst P,
                                                              uint32_t base, uint32_t n,
                                                              double* __restrict__ dist_out) {
   const uint32_t i0 = blockIdx.x * (2 * kEmThreads) + threadIdx.x;

@@ -88,6 +88,20 @@ __device__ __forceinline__ void em_block4(float& Y, float& comp, const Em4& E, f
   Y = t;
 }
 
+// em_block4 on two samples at once (component q is sample q), with the same
+// operations in the same order: each component is bit for bit em_block4's
+// result.  x - y is formed as fma(y, -1, x), which rounds identically.
+__device__ __forceinline__ void em_block4_2(float2& Y, float2& comp, float2 a, float2 negK4, float4 cz0,
+                                            float4 cz1) {
+  const float2 s4 = fma2(fma2(fma2(a, make_float2(cz0.x, cz1.x), make_float2(cz0.y, cz1.y)), a,
+                              make_float2(cz0.z, cz1.z)),
+                         a, make_float2(cz0.w, cz1.w));
+  const float2 y = fma2(comp, splat2(-1.0f), fma2(negK4, Y, s4));
+  const float2 t = add2(Y, y);
+  comp = fma2(y, splat2(-1.0f), fma2(Y, splat2(-1.0f), t));
+  Y = t;
+}
+
 // Simulate sample g and return rho; the summaries go to summ[j * summ_stride]
 // when summ is non-null.  X_s = th2 + Y_s with Y_0 = x0 - th2 split exactly
 // into (Y, -comp); observation steps are handled between runs of whole
@@ -172,6 +186,8 @@ __device__ __forceinline__ void ou_path2(const OUConst& P, const uint32_t g[2], 
     stream[q] = philox_stream(P.keys, g[q], P.sub, kTagPath);
     E4[q] = em4_constants(k[q]);
   }
+  const float2 a2 = make_float2(E4[0].a, E4[1].a);
+  const float2 negK4 = make_float2(-E4[0].K4, -E4[1].K4);
   const uint32_t S = P.n_steps;
   const uint32_t n_obs = P.n_obs;
   uint32_t s = 0, b = 0, j = 0;
@@ -179,11 +195,17 @@ __device__ __forceinline__ void ou_path2(const OUConst& P, const uint32_t g[2], 
     uint32_t s_next = P.s_obs[j];
     const uint32_t b_end = b + (s_next > s + 4u ? (s_next - s - 1u) >> 2 : 0u);
     s += (b_end - b) << 2;
-    for (; b < b_end; ++b) {
-      const float4 z0 = scaled_normals_of(philox_block(stream[0], P.keys, b), c[0]);
-      const float4 z1 = scaled_normals_of(philox_block(stream[1], P.keys, b), c[1]);
-      em_block4(Y[0], comp[0], E4[0], z0);
-      em_block4(Y[1], comp[1], E4[1], z1);
+    if (b < b_end) {
+      float2 Y2 = make_float2(Y[0], Y[1]), comp2 = make_float2(comp[0], comp[1]);
+      for (; b < b_end; ++b) {
+        const float4 z0 = scaled_normals_of(philox_block(stream[0], P.keys, b), c[0]);
+        const float4 z1 = scaled_normals_of(philox_block(stream[1], P.keys, b), c[1]);
+        em_block4_2(Y2, comp2, a2, negK4, z0, z1);
+      }
+      Y[0] = Y2.x;
+      Y[1] = Y2.y;
+      comp[0] = comp2.x;
+      comp[1] = comp2.y;
     }
     const float4 z0 = scaled_normals_of(philox_block(stream[0], P.keys, b), c[0]);
     const float4 z1 = scaled_normals_of(philox_block(stream[1], P.keys, b), c[1]);
