@@ -245,21 +245,32 @@ def profiled_traffic(n_samples):
     return float(rec["dram_bytes"]) * n_samples / float(rec["n_samples"])
 
 
-def issue_bound(ms_per_launch, path_steps):
-    """The instruction-issue ceiling of the kernel from its measured
-    instructions per path-step (committed ncu summary), None if absent."""
+def pipe_bounds(ms_per_launch, path_steps):
+    """The per-pipe ceilings of the kernel from its measured cycles per warp
+    step (32 path-steps) on one SM sub-partition -- issue slots, ALU-pipe
+    cycles, FMA-pipe cycles -- read from the committed ncu summary; None if
+    absent or the kernel changed since.  Each ceiling is the path-step rate if
+    that resource alone were busy all the time."""
     path = os.path.join(ROOT, "profiles", "em_ou_fused_traffic.json")
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    ipp = rec.get("instructions_per_path_step")
-    if not ipp or rec.get("source_hash") != kernel_source_hash():
+    cyc = rec.get("smsp_cycles_per_warp_step")
+    if not cyc or rec.get("source_hash") != kernel_source_hash():
         return None
-    ceiling = SM_COUNT * 128 * SM_MAX_MHZ * 1e6 / ipp
     achieved = path_steps / (ms_per_launch / 1e3)
-    return {"instructions_per_path_step": ipp, "ceiling_path_steps_per_s": ceiling,
-            "frac": achieved / ceiling}
+    smsp_cycles_per_s = SM_COUNT * 4 * SM_MAX_MHZ * 1e6
+    out = {"cycles_per_warp_step": cyc}
+    for name, c in cyc.items():
+        if name == "elapsed":
+            continue
+        ceiling = smsp_cycles_per_s * 32 / c
+        out[name] = {"ceiling_path_steps_per_s": ceiling, "frac": achieved / ceiling}
+    binding = min((k for k in out if k != "cycles_per_warp_step"),
+                  key=lambda k: out[k]["ceiling_path_steps_per_s"])
+    out["binding"] = binding
+    return out
 
 
 def gpu_arm(args):
@@ -385,7 +396,7 @@ def gpu_arm(args):
             "peak_basis": "FP32+MUFU roofline: 2 MUFU ops/path-step (log,sqrt,sin,cos per pair), "
                           "16 MUFU/SM/clk x 152 SMs x 2070 MHz; FP32 pipe bound (6 ops/step, "
                           "128/SM/clk) is looser",
-            "issue_bound": issue_bound(statistics.mean(em_ms), abc_steps)}
+            "pipe_bounds": pipe_bounds(statistics.mean(em_ms), abc_steps)}
     clock = clocks.summary()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,

@@ -88,14 +88,28 @@ __device__ __forceinline__ void em_block4(float& Y, float& comp, const Em4& E, f
   Y = t;
 }
 
-// em_block4 on two samples at once (component q is sample q), with the same
-// operations in the same order: each component is bit for bit em_block4's
-// result.  x - y is formed as fma(y, -1, x), which rounds identically.
-__device__ __forceinline__ void em_block4_2(float2& Y, float2& comp, float2 a, float2 negK4, float4 cz0,
-                                            float4 cz1) {
-  const float2 s4 = fma2(fma2(fma2(a, make_float2(cz0.x, cz1.x), make_float2(cz0.y, cz1.y)), a,
-                              make_float2(cz0.z, cz1.z)),
-                         a, make_float2(cz0.w, cz1.w));
+// The four normals of counter block b for two samples at once, packed across
+// the samples (lane q = sample q): z[l] holds normal l of each, scaled by
+// c = (th3 sqrt(dt)) of each.  Bit for bit the values scaled_normals_of gives
+// each sample; the normals arrive paired for the packed EM update.
+__device__ __forceinline__ void scaled_normals_x2(uint4 w0, uint4 w1, float2 c, float2 z[4]) {
+  const float2 rA = mul2(c, sqrt_pos2(neg2_log_u01_2(w0.x, w1.x)));
+  float2 sA, cA;
+  sincos_2pi_u01_2(w0.y, w1.y, sA, cA);
+  const float2 rB = mul2(c, sqrt_pos2(neg2_log_u01_2(w0.z, w1.z)));
+  float2 sB, cB;
+  sincos_2pi_u01_2(w0.w, w1.w, sB, cB);
+  z[0] = mul2(rA, cA);
+  z[1] = mul2(rA, sA);
+  z[2] = mul2(rB, cB);
+  z[3] = mul2(rB, sB);
+}
+
+// em_block4 on two samples at once (lane q is sample q), with the same
+// operations in the same order: each lane is bit for bit em_block4's result.
+// x - y is formed as fma(y, -1, x), which rounds identically.
+__device__ __forceinline__ void em_block4_2(float2& Y, float2& comp, float2 a, float2 negK4, const float2 z[4]) {
+  const float2 s4 = fma2(fma2(fma2(a, z[0], z[1]), a, z[2]), a, z[3]);
   const float2 y = fma2(comp, splat2(-1.0f), fma2(negK4, Y, s4));
   const float2 t = add2(Y, y);
   comp = fma2(y, splat2(-1.0f), fma2(Y, splat2(-1.0f), t));
@@ -169,25 +183,26 @@ template <bool kWantSumm>
 __device__ __forceinline__ void ou_path2(const OUConst& P, const uint32_t g[2], const float th1[2],
                                          const float th2[2], const float th3[2], double* summ0,
                                          double* summ1, uint32_t summ_stride, double out[2]) {
-  float k[2], c[2], Y[2], comp[2];
+  float k[2], Y0[2], comp0[2];
   double th2d[2], acc[2];
   PhiloxStream stream[2];
   Em4 E4[2];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     k[q] = th1[q] * P.dt;
-    c[q] = th3[q] * P.sqrt_dt;
-    Y[q] = P.x0 - th2[q];
-    const float bb = Y[q] - P.x0;
-    const float err = (P.x0 - (Y[q] - bb)) + (-th2[q] - bb);
-    comp[q] = -err;
+    Y0[q] = P.x0 - th2[q];
+    const float bb = Y0[q] - P.x0;
+    const float err = (P.x0 - (Y0[q] - bb)) + (-th2[q] - bb);
+    comp0[q] = -err;
     th2d[q] = static_cast<double>(th2[q]);
     acc[q] = 0.0;
     stream[q] = philox_stream(P.keys, g[q], P.sub, kTagPath);
     E4[q] = em4_constants(k[q]);
   }
+  const float2 c = make_float2(th3[0] * P.sqrt_dt, th3[1] * P.sqrt_dt);
   const float2 a2 = make_float2(E4[0].a, E4[1].a);
   const float2 negK4 = make_float2(-E4[0].K4, -E4[1].K4);
+  float2 Y = make_float2(Y0[0], Y0[1]), comp = make_float2(comp0[0], comp0[1]);
   const uint32_t S = P.n_steps;
   const uint32_t n_obs = P.n_obs;
   uint32_t s = 0, b = 0, j = 0;
@@ -195,33 +210,25 @@ __device__ __forceinline__ void ou_path2(const OUConst& P, const uint32_t g[2], 
     uint32_t s_next = P.s_obs[j];
     const uint32_t b_end = b + (s_next > s + 4u ? (s_next - s - 1u) >> 2 : 0u);
     s += (b_end - b) << 2;
-    if (b < b_end) {
-      float2 Y2 = make_float2(Y[0], Y[1]), comp2 = make_float2(comp[0], comp[1]);
-      for (; b < b_end; ++b) {
-        const float4 z0 = scaled_normals_of(philox_block(stream[0], P.keys, b), c[0]);
-        const float4 z1 = scaled_normals_of(philox_block(stream[1], P.keys, b), c[1]);
-        em_block4_2(Y2, comp2, a2, negK4, z0, z1);
-      }
-      Y[0] = Y2.x;
-      Y[1] = Y2.y;
-      comp[0] = comp2.x;
-      comp[1] = comp2.y;
+    for (; b < b_end; ++b) {
+      float2 z[4];
+      scaled_normals_x2(philox_block(stream[0], P.keys, b), philox_block(stream[1], P.keys, b), c, z);
+      em_block4_2(Y, comp, a2, negK4, z);
     }
-    const float4 z0 = scaled_normals_of(philox_block(stream[0], P.keys, b), c[0]);
-    const float4 z1 = scaled_normals_of(philox_block(stream[1], P.keys, b), c[1]);
+    float2 z[4];
+    scaled_normals_x2(philox_block(stream[0], P.keys, b), philox_block(stream[1], P.keys, b), c, z);
     ++b;
-    const float zz0[4] = {z0.x, z0.y, z0.z, z0.w};
-    const float zz1[4] = {z1.x, z1.y, z1.z, z1.w};
+    float Ys[2] = {Y.x, Y.y}, Cs[2] = {comp.x, comp.y};
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       if (s < S) {
-        em_step(Y[0], comp[0], k[0], zz0[l]);
-        em_step(Y[1], comp[1], k[1], zz1[l]);
+        em_step(Ys[0], Cs[0], k[0], z[l].x);
+        em_step(Ys[1], Cs[1], k[1], z[l].y);
         ++s;
         if (s == s_next) {
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
-            const double x = th2d[q] + (static_cast<double>(Y[q]) - static_cast<double>(comp[q]));
+            const double x = th2d[q] + (static_cast<double>(Ys[q]) - static_cast<double>(Cs[q]));
             const double r = x - P.y[j];
             acc[q] = fma(r, r, acc[q]);
             if (kWantSumm) (q ? summ1 : summ0)[static_cast<size_t>(j) * summ_stride] = x;
@@ -231,6 +238,8 @@ __device__ __forceinline__ void ou_path2(const OUConst& P, const uint32_t g[2], 
         }
       }
     }
+    Y = make_float2(Ys[0], Ys[1]);
+    comp = make_float2(Cs[0], Cs[1]);
   }
   out[0] = sqrt(acc[0]);
   out[1] = sqrt(acc[1]);

@@ -5,8 +5,8 @@
 //   z_t = normal t of stream (seed, m, k, PATH), t = 0..n_obs,
 //   ybar = lambda_k z_0 + (1/n_obs) sum_{t>=1} z_t,
 //   counts[k] += [|ybar| >= |ybar_obs|].
-// One thread walks a strided set of data sets of one lambda (blockIdx.y) and
-// keeps its count in a register; a warp reduction and one 64-bit atomic per
+// One thread walks a strided set of data-set pairs of one lambda (blockIdx.y)
+// and keeps its count in a register; a warp reduction and one 64-bit atomic per
 // warp add it to counts[k].  ybar comes from dataset_ybar (binary32 normals,
 // Kahan-compensated sum, binary64 ybar); the comparison is binary64.
 #include "internal.h"
@@ -29,14 +29,23 @@ __global__ void __launch_bounds__(kPvThreads) pvalue_tail(const double* __restri
   const uint32_t k = blockIdx.y;
   const double lam = lambda[k];
   unsigned int count = 0;
-  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kPvThreads;
-  for (uint64_t m0 = static_cast<uint64_t>(blockIdx.x) * kPvThreads; m0 < m_sets; m0 += stride) {
-    const uint64_t m = m0 + threadIdx.x;
-    if (m < m_sets) {
-      const double ybar = dataset_ybar(K, lam, n_obs, inv_n, set_base + static_cast<uint32_t>(m), k,
-                                       kTagPath);
-      if (kWantYbar) ybar_out[static_cast<size_t>(k) * m_sets + m] = ybar;
-      count += (fabs(ybar) >= abs_ybar_obs) ? 1u : 0u;
+  // Each thread takes data sets m and m + kPvThreads of a 2 kPvThreads chunk,
+  // evaluated together (dataset_ybar2); past the end the second lane repeats
+  // the first and is not counted.
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * (2 * kPvThreads);
+  for (uint64_t m0 = static_cast<uint64_t>(blockIdx.x) * (2 * kPvThreads); m0 < m_sets; m0 += stride) {
+    const uint64_t ma = m0 + threadIdx.x;
+    const uint64_t mb = ma + kPvThreads;
+    if (ma < m_sets) {
+      const uint64_t mb_eff = mb < m_sets ? mb : ma;
+      const double2 yb = dataset_ybar2(K, lam, n_obs, inv_n, set_base + static_cast<uint32_t>(ma),
+                                       set_base + static_cast<uint32_t>(mb_eff), k, kTagPath);
+      if (kWantYbar) ybar_out[static_cast<size_t>(k) * m_sets + ma] = yb.x;
+      count += (fabs(yb.x) >= abs_ybar_obs) ? 1u : 0u;
+      if (mb < m_sets) {
+        if (kWantYbar) ybar_out[static_cast<size_t>(k) * m_sets + mb] = yb.y;
+        count += (fabs(yb.y) >= abs_ybar_obs) ? 1u : 0u;
+      }
     }
   }
   count = __reduce_add_sync(0xFFFFFFFFu, count);
@@ -64,7 +73,7 @@ cudaError_t launch_pvalue(const double* lambda, uint32_t n_lambda, uint32_t n_ob
   // About four waves of 8 resident CTAs per SM over the whole sweep.
   const uint64_t target = static_cast<uint64_t>(sms) * 8u * 4u;
   uint64_t bx = (target + n_lambda - 1) / n_lambda;
-  const uint64_t need = (static_cast<uint64_t>(m_sets) + kPvThreads - 1) / kPvThreads;
+  const uint64_t need = (static_cast<uint64_t>(m_sets) + 2 * kPvThreads - 1) / (2 * kPvThreads);
   if (bx > need) bx = need;
   if (bx < 1) bx = 1;
   const dim3 grid(static_cast<unsigned>(bx), n_lambda);

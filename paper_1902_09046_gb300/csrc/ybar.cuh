@@ -49,4 +49,65 @@ __device__ __forceinline__ double dataset_ybar(const PhiloxKeys& K, double lam, 
   return fma(lam, static_cast<double>(z0), sum * inv_n);
 }
 
+// Two data sets at once (lane q = data set q, streams S0 and S1 of the same
+// length): the normals come packed across the sets and the Kahan sums run on
+// packed pairs, with kahan_add's operations in its order (x - y formed as
+// fma(y, -1, x), which rounds identically), so each lane is bit for bit
+// dataset_ybar of its set.
+__device__ __forceinline__ void normals_x2(uint4 w0, uint4 w1, float2 z[4]) {
+  const float2 rA = sqrt_pos2(neg2_log_u01_2(w0.x, w1.x));
+  float2 sA, cA;
+  sincos_2pi_u01_2(w0.y, w1.y, sA, cA);
+  const float2 rB = sqrt_pos2(neg2_log_u01_2(w0.z, w1.z));
+  float2 sB, cB;
+  sincos_2pi_u01_2(w0.w, w1.w, sB, cB);
+  z[0] = mul2(rA, cA);
+  z[1] = mul2(rA, sA);
+  z[2] = mul2(rB, cB);
+  z[3] = mul2(rB, sB);
+}
+
+__device__ __forceinline__ void kahan_add2(float2& s, float2& comp, float2 x) {
+  const float2 y = fma2(comp, splat2(-1.0f), x);
+  const float2 t = add2(s, y);
+  comp = fma2(y, splat2(-1.0f), fma2(s, splat2(-1.0f), t));
+  s = t;
+}
+
+__device__ __forceinline__ double2 dataset_ybar2(const PhiloxKeys& K, double lam, uint32_t n_obs,
+                                                 double inv_n, uint32_t c1a, uint32_t c1b, uint32_t c2,
+                                                 uint32_t tag) {
+  const PhiloxStream S0 = philox_stream(K, c1a, c2, tag);
+  const PhiloxStream S1 = philox_stream(K, c1b, c2, tag);
+  const uint32_t n_full = (n_obs + 1) >> 2;
+  const uint32_t rem = (n_obs + 1) & 3u;
+  float2 z0 = splat2(0.0f), s = splat2(0.0f), comp = splat2(0.0f);
+  float2 z[4];
+  for (uint32_t b = 0; b < n_full; ++b) {
+    normals_x2(philox_block(S0, K, b), philox_block(S1, K, b), z);
+    if (b == 0) {
+      z0 = z[0];
+    } else {
+      kahan_add2(s, comp, z[0]);
+    }
+    kahan_add2(s, comp, z[1]);
+    kahan_add2(s, comp, z[2]);
+    kahan_add2(s, comp, z[3]);
+  }
+  if (rem) {
+    normals_x2(philox_block(S0, K, n_full), philox_block(S1, K, n_full), z);
+    if (n_full == 0) {
+      z0 = z[0];
+    } else {
+      kahan_add2(s, comp, z[0]);
+    }
+    if (rem > 1) kahan_add2(s, comp, z[1]);
+    if (rem > 2) kahan_add2(s, comp, z[2]);
+  }
+  const double sum0 = static_cast<double>(s.x) - static_cast<double>(comp.x);
+  const double sum1 = static_cast<double>(s.y) - static_cast<double>(comp.y);
+  return make_double2(fma(lam, static_cast<double>(z0.x), sum0 * inv_n),
+                      fma(lam, static_cast<double>(z0.y), sum1 * inv_n));
+}
+
 }  // namespace ppabc
