@@ -50,7 +50,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--mode", choices=("path", "batch", "serve", "toggle", "configs"), default="path",
+    ap.add_argument("--mode", choices=("path", "batch", "serve", "toggle", "configs", "bege"), default="path",
                     help="path: the headline step; batch: 256 uneven jobs, plain vs persistent; "
                          "serve: Poisson arrivals, served vs plain")
     ap.add_argument("--jobs", type=int, default=256)
@@ -628,6 +628,95 @@ def toggle_mode(args):
     return 0
 
 
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (nominal; not in the measured peaks)
+
+
+def bege_profile(launch_ms):
+    """FP64 operations per bege_density launch from the committed ncu summary
+    (DFMA counted twice), as achieved TFLOP/s; None if absent or stale."""
+    path = os.path.join(ROOT, "profiles", "bege_density_counts.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for rel in BEGE_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    if rec.get("source_hash") != h.hexdigest()[:16]:
+        return None
+    return rec["fp64_flops_per_launch"] / (launch_ms / 1e3) / 1e12, rec
+
+
+BEGE_SOURCES = ("paper_1902_09046_gb300/csrc/bege.cu",)
+
+
+def bege_mode(args):
+    """BEGE log-likelihoods (Sec. 4.3) of 1024 particles on a 1099-month
+    return series, as in one SMC iteration of the paper's BEGE inference:
+    particle-months per second, for particles drawn from the prior (the first
+    iteration) and particles concentrated around a plausible parameter vector
+    (a later iteration)."""
+    import torch
+    from paper_1902_09046_gb300 import binding
+    from paper_1902_09046_gb300 import build as libbuild
+
+    torch.cuda.set_device(0)
+    libbuild.build()
+    binding.device_check()
+    r_np = workloads.bege_returns()
+    T, n_p, h = len(r_np), workloads.BEGE_N_PARTICLES, workloads.BEGE_H
+    sets = {"later": workloads.bege_particles(n_p, seed=6, centre=workloads.BEGE_THETA_REF, rel_spread=0.05),
+            "prior": workloads.bege_particles(n_p, seed=6)}
+    r = torch.from_numpy(r_np).cuda()
+    stream = torch.cuda.current_stream()
+    res = {}
+    with ClockSampler(0) as clocks:
+        for name, th_np in sets.items():
+            th = torch.from_numpy(th_np).cuda()
+            out = binding.bege_loglik(th, r, h)
+            for _ in range(max(3, args.warmup)):
+                binding.bege_loglik(th, r, h, out=out)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            for a, b in ev:
+                a.record(stream)
+                binding.bege_loglik(th, r, h, out=out)
+                b.record(stream)
+            torch.cuda.synchronize()
+            ms = statistics.median([a.elapsed_time(b) for a, b in ev])
+            ll = out["ll"].cpu().numpy()
+            res[name] = {"ms": ms, "particle_steps_per_s": n_p * T / (ms / 1e3),
+                         "finite": int(np.isfinite(ll).sum())}
+    main = res["later"]
+    prof = bege_profile(main["ms"])
+    roof = {"kernel": "bege_density", "bound": "fp64", "unit": "TFLOP/s",
+            "peak": FP64_NOMINAL_TFLOPS, "peak_basis": "nominal GB300 dense FP64 (of nominal)",
+            "achieved": prof[0] if prof else None, "frac": prof[0] / FP64_NOMINAL_TFLOPS if prof else None,
+            "traffic": None}
+    line = {"mode": "bege", "metric": "BEGE log-likelihood particle-months/s", "unit": "particle-steps/s",
+            "value": main["particle_steps_per_s"], "ms_per_run": main["ms"], "higher_is_better": True,
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "steps": args.steps,
+            "runs": res, "roofline": roof,
+            "config": {"workload": f"BEGE log-likelihood, {n_p} particles x T={T} months, N_w=100, h={h:g}; "
+                                   "'later' = particles within 5% of the prior box around a plausible "
+                                   "vector, 'prior' = prior draws"},
+            "clocks": clocks.summary()}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        thr = oracle.default_threads()
+        n_cpu = 4 * thr
+        t0 = time.perf_counter()
+        oracle.bege_loglik(sets["later"][:, :n_cpu], r_np, h, n_threads=thr)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": n_cpu * T / dt, "unit": "particle-steps/s", "cores": thr,
+                                "kind": "oracle", "sample": f"{n_cpu} of the 1024 'later' particles, FP64, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def configs_mode(args):
     """Each synthetic configuration timed on its own (GPU, CUDA events, median
     of --steps after warm-up), with the oracle on a bounded sample of it."""
@@ -723,6 +812,8 @@ def main():
         return serve_mode(args)
     if args.mode == "toggle":
         return toggle_mode(args)
+    if args.mode == "bege":
+        return bege_mode(args)
     if args.mode == "configs":
         return configs_mode(args)
     return gpu_arm(args)

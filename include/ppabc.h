@@ -504,6 +504,45 @@ int weakinf_test(const double *lambda, uint32_t n_lambda, double lambda0,
                  uint32_t n_obs, uint64_t n_sets, double alpha, uint64_t seed,
                  double *gamma_out, uint32_t *counts_out, void *stream);
 
+/* BEGE likelihood limits and constants. */
+#define PPABC_BEGE_NPAR 11
+#define PPABC_BEGE_NW 100
+#define PPABC_BEGE_MAX_PARTICLES (1 << 20)
+#define PPABC_BEGE_MAX_T (1 << 16)
+
+/*
+ * BEGE log-likelihood (Sec. 4.3: the BEGE model of monthly return
+ * innovations, its shape recursion, Eq. BEGE_LL, the distribution function
+ * Eq. CDF_BEGE discretised as Eq. BEGE_LL_approx, P(a, x) of Eq. incompGamma)
+ * for n_particles parameter vectors on one return series r_1..r_T.
+ * Particle i has theta = (p0, sigma_p, rho_p, phi_p+, phi_p-, n0, sigma_n,
+ * rho_n, phi_n+, phi_n-, mu), row k of theta holding parameter k of every
+ * particle.  With u_t = r_t - mu:
+ *   ll_i = sum_{t=1..T} log f(u_t; sigma_p, sigma_n, p_{t-1}, n_{t-1}),
+ *   p_t = p0 + rho_p p_{t-1} + phi_p^{+|-} u_t^2 / (2 sigma_p^2)   (+ if u_t >= 0),
+ *   n_t likewise with sigma_n, rho_n, phi_n^{+|-};  (p_0, n_0) = (p0, n0),
+ *   f(u) = (F(u + h) - F(u - h)) / (2 h),
+ *   F(u) = sum_{j=1..100} [1 - P(n, (w_{j-1} - u + n sigma_n) / sigma_n)]
+ *                          [P(p, (w_j + p sigma_p) / sigma_p) - P(p, (w_{j-1} + p sigma_p) / sigma_p)],
+ *   w_j = w_0 + j dw,  w_0 = 1e-4 - p sigma_p,  dw = (10 sigma_p sqrt(p) - w_0) / 99,
+ * P(a, x) the regularised lower incomplete gamma (0 for x <= 0): its power
+ * series for x < a + 1 and Legendre's continued fraction for the complement
+ * otherwise.  A scale or shape <= 0, or a density that is not a positive
+ * finite number, gives ll_i = -inf.  All arithmetic is binary64.
+ *   theta      [11][n_particles] double (device).
+ *   r          [T] double (device): the returns r_1..r_T.
+ *   h          finite-difference step, 0 < h < 1.
+ *   ll_out     [n_particles] double (device).
+ *   logf_out   nullable [n_particles][T] double (device): log f per step
+ *              (NaN after the step that ended a particle).
+ *   workspace  bege_loglik_workspace_bytes(n_particles, T) bytes, 256-byte aligned.
+ * Requires 1 <= n_particles <= PPABC_BEGE_MAX_PARTICLES, 1 <= T <= PPABC_BEGE_MAX_T.
+ */
+size_t bege_loglik_workspace_bytes(uint64_t n_particles, uint32_t T);
+int bege_loglik(const double *theta, uint64_t n_particles, const double *r, uint32_t T, double h,
+                double *ll_out, double *logf_out, void *workspace, size_t workspace_bytes,
+                void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,6 +91,14 @@ def _load():
             lib.orc_toggle_prior_predictive.restype = i32
             lib.orc_recalibrate.argtypes = [P, P, u64, u32, P, u64, u64, P, P, i32]
             lib.orc_recalibrate.restype = i32
+            lib.orc_gammainc_p.argtypes = [dbl, dbl]
+            lib.orc_gammainc_p.restype = dbl
+            lib.orc_bege_cdf.argtypes = [dbl, dbl, dbl, dbl, dbl]
+            lib.orc_bege_cdf.restype = dbl
+            lib.orc_bege_density.argtypes = [dbl, dbl, dbl, dbl, dbl, dbl]
+            lib.orc_bege_density.restype = dbl
+            lib.orc_bege_loglik.argtypes = [P, u64, P, u32, dbl, P, P, i32]
+            lib.orc_bege_loglik.restype = i32
             _lib = lib
     return _lib
 
@@ -254,3 +262,48 @@ def recalibrate(summ: np.ndarray, theta: np.ndarray, acc: np.ndarray, k: int,
     if rc != 0:
         raise ValueError("oracle rejected the recalibration arguments")
     return u, rc_out
+
+
+BEGE_NPAR = 11
+BEGE_NW = 100
+BEGE_PARAMS = ("p0", "sigma_p", "rho_p", "phi_p_plus", "phi_p_minus",
+               "n0", "sigma_n", "rho_n", "phi_n_plus", "phi_n_minus", "mu")
+
+
+def gammainc_p(a, x) -> np.ndarray:
+    """Regularised lower incomplete gamma P(a, x), elementwise."""
+    A, X = np.broadcast_arrays(np.asarray(a, dtype=np.float64), np.asarray(x, dtype=np.float64))
+    f = _load().orc_gammainc_p
+    return np.array([f(float(ai), float(xi)) for ai, xi in zip(A.ravel(), X.ravel())]).reshape(A.shape)
+
+
+def bege_cdf(u, sp: float, sn: float, p: float, n: float) -> np.ndarray:
+    """The discretised BEGE distribution function at each u."""
+    f = _load().orc_bege_cdf
+    U = np.asarray(u, dtype=np.float64)
+    return np.array([f(float(v), sp, sn, p, n) for v in U.ravel()]).reshape(U.shape)
+
+
+def bege_density(u, sp: float, sn: float, p: float, n: float, h: float) -> np.ndarray:
+    """The BEGE density at each u by central differences with step h."""
+    f = _load().orc_bege_density
+    U = np.asarray(u, dtype=np.float64)
+    return np.array([f(float(v), sp, sn, p, n, h) for v in U.ravel()]).reshape(U.shape)
+
+
+def bege_loglik(theta: np.ndarray, r: np.ndarray, h: float, want_dens: bool = False,
+                n_threads: int | None = None):
+    """theta [11, np] float64 (rows in BEGE_PARAMS order), r [T] -> ll [np]
+    (and, with want_dens, the densities [np, T])."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    rr = np.ascontiguousarray(r, dtype=np.float64)
+    if th.ndim != 2 or th.shape[0] != BEGE_NPAR:
+        raise ValueError("theta must be [11, np]")
+    n_p, T = th.shape[1], rr.shape[0]
+    ll = np.zeros(n_p)
+    dens = np.zeros((n_p, T)) if want_dens else None
+    rc = _load().orc_bege_loglik(_ptr(th), n_p, _ptr(rr), T, h, _ptr(ll), _ptr(dens),
+                                 n_threads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle rejected the BEGE arguments")
+    return (ll, dens) if want_dens else ll

@@ -140,6 +140,21 @@ int orc_recalibrate(const double *summ, const float *theta, uint64_t n, uint32_t
                     const uint32_t *acc, uint64_t q, uint64_t k, double *u, float *theta_rc,
                     int n_threads);
 
+/* BEGE log-likelihood (Sec. 4.3).  theta is [ORC_BEGE_NPAR][np] (row k =
+ * parameter k of every particle) in the order (p0, sigma_p, rho_p, phi_p+,
+ * phi_p-, n0, sigma_n, rho_n, phi_n+, phi_n-, mu); r holds r_1..r_T; the
+ * density is the central difference of the discretised distribution function
+ * with step h.  ll[np] gets each log-likelihood (-inf where a scale, a shape
+ * or a density is not positive); dens[np][T], if non-NULL, the densities
+ * (NaN after the step that ended a particle). */
+#define ORC_BEGE_NPAR 11
+#define ORC_BEGE_NW 100
+double orc_gammainc_p(double a, double x);
+double orc_bege_cdf(double u, double sp, double sn, double p, double n);
+double orc_bege_density(double u, double sp, double sn, double p, double n, double h);
+int orc_bege_loglik(const double *theta, uint64_t np, const double *r, uint32_t T, double h,
+                    double *ll, double *dens, int n_threads);
+
 #ifdef __cplusplus
 }
 #endif

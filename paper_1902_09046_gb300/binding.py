@@ -41,7 +41,7 @@ EXPORTED = ("ppabc_abi_version", "ppabc_last_error", "ppabc_device_check", "ppab
             "ppabc_server_release", "ppabc_server_cancel", "ppabc_server_get_stats",
             "ppabc_server_now", "ppabc_server_destroy", "weakinf_test", "toggle_prior_predictive",
             "abc_rejection_workspace_bytes", "abc_rejection", "abc_recalibrate_workspace_bytes",
-            "abc_recalibrate")
+            "abc_recalibrate", "bege_loglik_workspace_bytes", "bege_loglik")
 WEAKINF_MAX_SETS = 16384
 PPABC_PENDING = 1
 JOB_ABC = 0
@@ -185,6 +185,8 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
             "abc_rejection": ([M, P, dbl, u64, u64, u64, u64, u32, P, P, P, P, sz, P], i32),
             "abc_recalibrate_workspace_bytes": ([u64, u64], sz),
             "abc_recalibrate": ([P, P, u64, u32, P, u64, u64, P, P, P, sz, P], i32),
+            "bege_loglik_workspace_bytes": ([u64, u32], sz),
+            "bege_loglik": ([P, u64, P, u32, dbl, P, P, P, sz, P], i32),
             "toggle_prior_predictive": ([ctypes.POINTER(ToggleModel), P, u64, u64, u64, u32, P, P,
                                          P, P, P], i32),
         }
@@ -382,6 +384,31 @@ def abc_recalibrate(summ: torch.Tensor, theta: torch.Tensor, acc_idx: torch.Tens
     _check(lib.abc_recalibrate(_ptr(summ), _ptr(theta), n, n_obs, _ptr(acc_idx), q, k, _ptr(u), _ptr(rc),
                                _ptr(ws), ws_bytes, _stream(stream)))
     return {"u": u, "theta_rc": rc}
+
+
+def bege_loglik(theta: torch.Tensor, r: torch.Tensor, h: float, want_logf: bool = False,
+                out: dict | None = None, stream=None) -> dict:
+    """theta [11, np] f64, r [T] f64 (CUDA) -> {"ll": [np] f64, "logf": [np, T] f64 | None}.
+    Pass out={"ll": ..., "ws": ...} to reuse buffers."""
+    if theta.dtype != torch.float64 or theta.dim() != 2 or theta.shape[0] != 11:
+        raise ValueError("theta must be a [11, np] float64 tensor")
+    if r.dtype != torch.float64 or r.dim() != 1:
+        raise ValueError("r must be a [T] float64 tensor")
+    n_p, T = theta.shape[1], r.shape[0]
+    dev = theta.device
+    lib = load_library()
+    out = dict(out or {})
+    ll = out.get("ll")
+    if ll is None:
+        ll = torch.empty(n_p, dtype=torch.float64, device=dev)
+    ws_bytes = int(lib.bege_loglik_workspace_bytes(n_p, T))
+    ws = out.get("ws")
+    if ws is None or ws.numel() < ws_bytes:
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    logf = torch.empty((n_p, T), dtype=torch.float64, device=dev) if want_logf else None
+    _check(lib.bege_loglik(_ptr(theta), n_p, _ptr(r), T, float(h), _ptr(ll), _ptr(logf), _ptr(ws),
+                           ws.numel(), _stream(stream)))
+    return {"ll": ll, "logf": logf, "ws": ws}
 
 
 def pvalue_sweep(lambdas: torch.Tensor, n_obs: int, m_sets: int, ybar_obs: float, seed: int,

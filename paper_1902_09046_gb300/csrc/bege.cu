@@ -1,0 +1,261 @@
+// bege.cu -- BEGE log-likelihood of many parameter vectors on one return
+// series (Sec. 4.3: the BEGE model, its shape recursion, Eq. BEGE_LL,
+// Eq. CDF_BEGE discretised as Eq. BEGE_LL_approx, P(a, x) of Eq. incompGamma).
+//
+// For particle i with theta = (p0, sp, rho_p, phi_p+, phi_p-, n0, sn, rho_n,
+// phi_n+, phi_n-, mu) and returns r_1..r_T:
+//   u_t = r_t - mu,  ll_i = sum_t log f(u_t; sp, sn, p_{t-1}, n_{t-1}),
+//   p_t = p0 + rho_p p_{t-1} + phi_p^{+|-} u_t^2 / (2 sp^2), (p_0, n_0) = (p0, n0),
+//   f(u) = (F(u + h) - F(u - h)) / (2h),
+//   F(u) = sum_{j=1..100} [1 - P(n, (w_{j-1} - u + n sn) / sn)]
+//                         [P(p, (w_j + p sp) / sp) - P(p, (w_{j-1} + p sp) / sp)],
+//   w_j = w_0 + j dw, w_0 = 1e-4 - p sp, dw = (10 sp sqrt(p) - w_0) / 99.
+//
+// The paper vectorises P(a, x) over a block of V grid nodes on one core.
+// Here three kernels split the work: the shape recursion (sequential in t,
+// one thread per particle), the densities (one warp per (particle, t): the
+// 101 grid nodes spread over the lanes, lgamma of the two shapes computed
+// once per warp, the grid differences taken with shuffles), and a fixed-order
+// reduction of log f over t per particle.  Everything is binary64: the
+// central difference divides the rounding of F by 2h.
+#include "internal.h"
+
+namespace ppabc {
+
+namespace {
+
+constexpr int kBegeNw = PPABC_BEGE_NW;  // grid intervals
+constexpr int kBegeWarpsPerCta = 8;
+constexpr double kGammaEps = 1e-17;
+constexpr double kGammaTiny = 1e-300;
+constexpr int kGammaMaxIter = 1000000;
+
+inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+struct BegeLayout {
+  size_t shape_p, shape_n, first_bad, logf, total;
+  BegeLayout(uint64_t np, uint64_t T) {
+    size_t o = 0;
+    shape_p = o;
+    o = align256(o + sizeof(double) * np * T);
+    shape_n = o;
+    o = align256(o + sizeof(double) * np * T);
+    first_bad = o;
+    o = align256(o + sizeof(uint32_t) * np);
+    logf = o;
+    o = align256(o + sizeof(double) * np * T);
+    total = o;
+  }
+};
+
+// Regularised lower incomplete gamma P(a, x), a > 0, with lga = lgamma(a):
+// the power series sum_j x^j / (a (a+1) ... (a+j)) times exp(-x + a ln x -
+// lga) for x < a + 1; for x >= a + 1, 1 - Q with Q from Legendre's continued
+// fraction (modified Lentz).  Each loop is bounded by kGammaMaxIter terms.
+__device__ double gammainc_p(double a, double lga, double x) {
+  if (!(x > 0.0)) return 0.0;
+  const double lead = -x + a * log(x) - lga;
+  if (x < a + 1.0) {
+    double ap = a, term = 1.0 / a, sum = term;
+    for (int k = 1; k < kGammaMaxIter; ++k) {
+      ap += 1.0;
+      term *= x / ap;
+      sum += term;
+      if (fabs(term) < fabs(sum) * kGammaEps) break;
+    }
+    return sum * exp(lead);
+  }
+  double b = x + 1.0 - a;
+  double c = 1.0 / kGammaTiny;
+  double d = 1.0 / b;
+  double h = d;
+  for (int i = 1; i < kGammaMaxIter; ++i) {
+    const double an = -i * (i - a);
+    b += 2.0;
+    d = fma(an, d, b);
+    if (fabs(d) < kGammaTiny) d = kGammaTiny;
+    c = b + an / c;
+    if (fabs(c) < kGammaTiny) c = kGammaTiny;
+    d = 1.0 / d;
+    const double del = d * c;
+    h *= del;
+    if (fabs(del - 1.0) < kGammaEps) break;
+  }
+  return 1.0 - exp(lead) * h;
+}
+
+// Shapes used at each step, one thread per particle; first_bad[i] = the first
+// step whose scale or shape is not positive (T if none).
+__global__ void bege_shapes(const double* __restrict__ theta, uint32_t np, const double* __restrict__ r,
+                            uint32_t T, double* __restrict__ shape_p, double* __restrict__ shape_n,
+                            uint32_t* __restrict__ first_bad) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const double p0 = theta[i], sp = theta[np + i], rp = theta[2ull * np + i];
+  const double fpp = theta[3ull * np + i], fpm = theta[4ull * np + i];
+  const double n0 = theta[5ull * np + i], sn = theta[6ull * np + i], rn = theta[7ull * np + i];
+  const double fnp = theta[8ull * np + i], fnm = theta[9ull * np + i], mu = theta[10ull * np + i];
+  uint32_t bad = T;
+  if (!(sp > 0.0) || !(sn > 0.0)) bad = 0;
+  double p = p0, n = n0;
+  const double inv2sp2 = 1.0 / (2.0 * sp * sp), inv2sn2 = 1.0 / (2.0 * sn * sn);
+  for (uint32_t t = 0; t < T && bad == T; ++t) {
+    if (!(p > 0.0) || !(n > 0.0)) {
+      bad = t;
+      break;
+    }
+    shape_p[static_cast<size_t>(i) * T + t] = p;
+    shape_n[static_cast<size_t>(i) * T + t] = n;
+    const double u = r[t] - mu;
+    const double u2 = u * u;
+    p = p0 + rp * p + (u >= 0.0 ? fpp : fpm) * inv2sp2 * u2;
+    n = n0 + rn * n + (u >= 0.0 ? fnp : fnm) * inv2sn2 * u2;
+  }
+  first_bad[i] = bad;
+}
+
+// log f(u_t) for task (i, t) per warp.  Lane l owns grid nodes j = l + 32 k,
+// k = 0..3 (j <= 100): it evaluates P(p, .) at w_j and, for j >= 1, the
+// two P(n, .) at w_{j-1} - (u +- h); the difference P(p, w_j) - P(p, w_{j-1})
+// takes w_{j-1}'s value from the neighbouring lane.
+__global__ void __launch_bounds__(32 * kBegeWarpsPerCta)
+bege_density(const double* __restrict__ theta, uint32_t np, const double* __restrict__ r, uint32_t T,
+             double h, const double* __restrict__ shape_p, const double* __restrict__ shape_n,
+             const uint32_t* __restrict__ first_bad, double* __restrict__ logf) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t n_tasks = static_cast<uint64_t>(np) * T;
+  const uint64_t warp0 = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t n_warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t task = warp0; task < n_tasks; task += n_warps) {
+    const uint32_t i = static_cast<uint32_t>(task / T);
+    const uint32_t t = static_cast<uint32_t>(task % T);
+    if (t >= first_bad[i]) continue;  // the whole warp skips together
+    const double sp = theta[np + i], sn = theta[6ull * np + i], mu = theta[10ull * np + i];
+    const double p = shape_p[task], n = shape_n[task];
+    const double u = r[t] - mu;
+    // lgamma of the two shapes, once per warp.
+    const double lg_own = lgamma(lane == 0 ? p : n);
+    const double lgp = __shfl_sync(0xFFFFFFFFu, lg_own, 0);
+    const double lgn = __shfl_sync(0xFFFFFFFFu, lg_own, 1);
+    const double w0 = 1e-4 - p * sp;
+    const double dw = (10.0 * sp * sqrt(p) - w0) / static_cast<double>(kBegeNw - 1);
+    const double psp = p * sp, nsn = n * sn;
+    const double up = u + h, um = u - h;
+    double acc_p = 0.0, acc_m = 0.0;
+    double F_last = 0.0;  // F at node 32 k + 31 of the previous group (lane 31's value)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int j = static_cast<int>(lane) + 32 * k;
+      const bool live = j <= kBegeNw;
+      double F = 0.0;
+      if (live) F = gammainc_p(p, lgp, (w0 + static_cast<double>(j) * dw + psp) / sp);
+      double F_prev = __shfl_up_sync(0xFFFFFFFFu, F, 1);
+      if (lane == 0) F_prev = F_last;
+      F_last = __shfl_sync(0xFFFFFFFFu, F, 31);
+      if (live && j >= 1) {
+        const double wjm1 = w0 + static_cast<double>(j - 1) * dw;
+        const double xp = (wjm1 - up + nsn) / sn;
+        const double xm = (wjm1 - um + nsn) / sn;
+        const double Gp = xp > 0.0 ? gammainc_p(n, lgn, xp) : 0.0;
+        const double Gm = xm > 0.0 ? gammainc_p(n, lgn, xm) : 0.0;
+        const double dF = F - F_prev;
+        acc_p += (1.0 - Gp) * dF;
+        acc_m += (1.0 - Gm) * dF;
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      acc_p += __shfl_xor_sync(0xFFFFFFFFu, acc_p, off);
+      acc_m += __shfl_xor_sync(0xFFFFFFFFu, acc_m, off);
+    }
+    if (lane == 0) {
+      const double f = (acc_p - acc_m) / (2.0 * h);
+      logf[task] = (f > 0.0 && isfinite(f)) ? log(f) : -INFINITY;
+    }
+  }
+}
+
+// ll_i = sum_{t < T} log f, fixed-order tree per particle; -inf if a step
+// was invalid or a density was not positive.
+__global__ void __launch_bounds__(256) bege_reduce(const double* __restrict__ logf, uint32_t T,
+                                                   const uint32_t* __restrict__ first_bad,
+                                                   double* __restrict__ ll) {
+  __shared__ double part[256];
+  const uint32_t i = blockIdx.x;
+  if (first_bad[i] < T) {
+    if (threadIdx.x == 0) ll[i] = -INFINITY;
+    return;
+  }
+  double s = 0.0;
+  for (uint32_t t = threadIdx.x; t < T; t += 256) s += logf[static_cast<size_t>(i) * T + t];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < static_cast<unsigned>(w)) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ll[i] = part[0] != part[0] ? -INFINITY : part[0];
+}
+
+}  // namespace
+
+}  // namespace ppabc
+
+using namespace ppabc;
+
+extern "C" {
+
+size_t bege_loglik_workspace_bytes(uint64_t n_particles, uint32_t T) {
+  return BegeLayout(n_particles ? n_particles : 1, T ? T : 1).total;
+}
+
+int bege_loglik(const double* theta, uint64_t n_particles, const double* r, uint32_t T, double h,
+                double* ll_out, double* logf_out, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!theta || !r || !ll_out) return set_error(PPABC_EINVAL, "theta, r and ll_out must be non-NULL");
+  if (n_particles == 0 || n_particles > PPABC_BEGE_MAX_PARTICLES)
+    return set_error(PPABC_EINVAL, "n_particles must be in [1, %d]", PPABC_BEGE_MAX_PARTICLES);
+  if (T == 0 || T > PPABC_BEGE_MAX_T) return set_error(PPABC_EINVAL, "T must be in [1, %d]", PPABC_BEGE_MAX_T);
+  if (!(h > 0.0) || !(h < 1.0)) return set_error(PPABC_EINVAL, "h must be in (0, 1)");
+  const BegeLayout L(n_particles, T);
+  if (!workspace || workspace_bytes < L.total)
+    return set_error(PPABC_ENOMEM, "workspace needs %zu bytes, got %zu", L.total, workspace_bytes);
+  if (reinterpret_cast<uintptr_t>(workspace) & 255u) return set_error(PPABC_EINVAL, "workspace must be 256-byte aligned");
+  int rc = require_device();
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(workspace);
+  double* shape_p = reinterpret_cast<double*>(w + L.shape_p);
+  double* shape_n = reinterpret_cast<double*>(w + L.shape_n);
+  uint32_t* first_bad = reinterpret_cast<uint32_t*>(w + L.first_bad);
+  double* logf = logf_out ? logf_out : reinterpret_cast<double*>(w + L.logf);
+  const uint32_t np = static_cast<uint32_t>(n_particles);
+  cudaError_t e = cudaSuccess;
+  if (logf_out) {
+    // Steps after the one that ended a particle keep NaN.
+    e = cudaMemsetAsync(logf_out, 0xFF, sizeof(double) * n_particles * T, s);
+  }
+  if (e == cudaSuccess) {
+    bege_shapes<<<(np + 127) / 128, 128, 0, s>>>(theta, np, r, T, shape_p, shape_n, first_bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t tasks = n_particles * T;
+    const uint64_t per_cta = kBegeWarpsPerCta;
+    uint64_t blocks = (tasks + per_cta - 1) / per_cta;
+    const uint64_t cap = static_cast<uint64_t>(sms > 0 ? sms : 1) * 64;
+    if (blocks > cap) blocks = cap;
+    bege_density<<<static_cast<unsigned>(blocks), 32 * kBegeWarpsPerCta, 0, s>>>(
+        theta, np, r, T, h, shape_p, shape_n, first_bad, logf);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    bege_reduce<<<np, 256, 0, s>>>(logf, T, first_bad, ll_out);
+    e = cudaGetLastError();
+  }
+  return check_cuda(e, "bege_loglik");
+}
+
+}  // extern "C"

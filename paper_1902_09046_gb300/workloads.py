@@ -205,3 +205,53 @@ def toggle_observed_quantiles(seed: int = 7) -> np.ndarray:
     from scipy import stats
     levels = np.arange(1, 20) / 20.0
     return loc + 100.0 * stats.lognorm.ppf(levels, s=scale)
+
+
+# BEGE model (Sec. 4.3): parameter order and the paper's uniform prior box
+# (p0, sigma_p, rho_p, phi_p+, phi_p-, n0, sigma_n, rho_n, phi_n+, phi_n-, mu).
+BEGE_PARAMS = ("p0", "sigma_p", "rho_p", "phi_p_plus", "phi_p_minus",
+               "n0", "sigma_n", "rho_n", "phi_n_plus", "phi_n_minus", "mu")
+BEGE_PRIOR_LO = (1e-4, 1e-4, 1e-4, 1e-4, 1e-4, 1e-4, 1e-4, 1e-4, -0.2, 1e-4, -0.9)
+BEGE_PRIOR_HI = (0.5, 0.3, 0.99, 0.5, 0.5, 1.0, 0.3, 0.99, 0.1, 0.75, 0.9)
+BEGE_T = 1099          # months in the paper's return series
+BEGE_N_PARTICLES = 1024
+BEGE_H = 1e-5          # finite-difference step of the density
+
+
+def bege_returns(T: int = BEGE_T, seed: int = 5) -> np.ndarray:
+    """Synthetic monthly log returns standing in for the paper's S&P series
+    (which is not available): mean 0.0075, a two-state volatility regime
+    (0.04 calm, 0.09 turbulent, staying with probability 0.97) and Student-t
+    (5 degrees of freedom) shocks with a negative skew from a mixture."""
+    rng = np.random.default_rng(seed)
+    r = np.empty(T)
+    state = 0
+    for t in range(T):
+        if rng.uniform() > 0.97:
+            state = 1 - state
+        vol = 0.04 if state == 0 else 0.09
+        z = rng.standard_t(5) / np.sqrt(5.0 / 3.0)
+        if rng.uniform() < 0.05:
+            z -= 1.5
+        r[t] = 0.0075 + vol * z
+    return r
+
+
+def bege_particles(n: int = BEGE_N_PARTICLES, seed: int = 6, centre=None,
+                   rel_spread: float = 0.0) -> np.ndarray:
+    """[11, n] parameter vectors: uniform on the paper's prior box, or, with a
+    centre, uniform within +-rel_spread of the box width around it (clipped to
+    the box), like the particles of a later SMC iteration."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.array(BEGE_PRIOR_LO), np.array(BEGE_PRIOR_HI)
+    if centre is None:
+        return lo[:, None] + (hi - lo)[:, None] * rng.uniform(size=(11, n))
+    c = np.asarray(centre, dtype=np.float64)
+    half = rel_spread * (hi - lo)
+    a, b = np.maximum(lo, c - half), np.minimum(hi, c + half)
+    return a[:, None] + (b - a)[:, None] * rng.uniform(size=(11, n))
+
+
+# A parameter vector in the plausible region for monthly returns (used as the
+# centre of the later-iteration particle set).
+BEGE_THETA_REF = (0.3, 0.03, 0.6, 0.2, 0.3, 0.5, 0.04, 0.6, 0.02, 0.4, 0.008)

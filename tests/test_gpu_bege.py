@@ -1,0 +1,130 @@
+"""GPU parity of the BEGE log-likelihood (C ABI vs CPU oracle, both binary64).
+
+Tolerance: each side forms F(u +- h) as a sum of 100 products of incomplete
+gamma values.  Those carry the rounding of their exponent -x + a ln x -
+lnGamma(a), which the two sides evaluate with different libraries: about
+eps (x + a |ln x| + |lnGamma(a)|) relative, i.e. ~1e-15 for shapes near 1 and
+~1e-13 for shapes in the hundreds.  The central difference divides by 2h
+(h = 1e-5).  So step t allows
+  |d log f_t| <= 1e-13 (1 + s_t ln(2 + s_t)) / (h f_t),  s_t = p_{t-1} + n_{t-1},
+with f_t from the oracle, and a particle the sum of that plus 1e-12 |ll|."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import require_gpu, to_np, torch
+from paper_1902_09046_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+H = W.BEGE_H
+
+
+def _edge_particles():
+    """Columns that end early: zero scale, negative scale, a shape driven
+    below zero by phi_n+ < 0, and a tiny positive-shock scale whose grid
+    cannot reach the returns (f = 0)."""
+    ref = np.array(W.BEGE_THETA_REF)
+    cols = []
+    for k, v in ((1, 0.0), (6, -0.05)):
+        c = ref.copy()
+        c[k] = v
+        cols.append(c)
+    c = ref.copy()
+    c[8], c[6], c[7], c[5] = -0.2, 0.005, 0.0, 0.05
+    cols.append(c)
+    c = ref.copy()
+    c[1], c[0], c[6] = 1e-4, 1e-4, 1e-4
+    cols.append(c)
+    return np.stack(cols, axis=1)
+
+
+def _shape_sums(theta, r):
+    """p_{t-1} + n_{t-1} at every step (tolerance helper; NaN once invalid)."""
+    n_p, T = theta.shape[1], len(r)
+    out = np.full((n_p, T), np.nan)
+    for i in range(n_p):
+        p0, sp, rp, fpp, fpm, n0, sn, rn, fnp, fnm, mu = theta[:, i]
+        p, n = p0, n0
+        for t in range(T):
+            if not (p > 0 and n > 0 and sp > 0 and sn > 0):
+                break
+            out[i, t] = p + n
+            u = r[t] - mu
+            p = p0 + rp * p + (fpp if u >= 0 else fpm) * u * u / (2 * sp * sp)
+            n = n0 + rn * n + (fnp if u >= 0 else fnm) * u * u / (2 * sn * sn)
+    return out
+
+
+def _compare(theta, r, ll_gpu, logf_gpu=None):
+    ll_o, dens = oracle.bege_loglik(theta, r, H, want_dens=True)
+    fin_o = np.isfinite(ll_o)
+    np.testing.assert_array_equal(np.isfinite(ll_gpu), fin_o)
+    s_t = _shape_sums(theta, r)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tol_t = np.where(dens > 0, 1e-13 * (1 + s_t * np.log(2 + s_t)) / (H * dens), 0.0)
+    tol = np.nansum(tol_t, axis=1) + 1e-12 * np.abs(np.where(fin_o, ll_o, 0.0))
+    err = np.abs(ll_gpu - ll_o)
+    assert np.all(err[fin_o] <= tol[fin_o]), (err[fin_o].max(), tol[fin_o][np.argmax(err[fin_o])])
+    if logf_gpu is not None:
+        live = dens > 0
+        e = np.abs(logf_gpu[live] - np.log(dens[live]))
+        bad = np.flatnonzero(e > tol_t[live])
+        if bad.size:
+            w = bad[np.argsort(-(e[bad] / tol_t[live][bad]))[:5]]
+            raise AssertionError("per-step log f outside tolerance: " + "; ".join(
+                f"f={dens[live][k]:.4g} s={s_t[live][k]:.4g} err={e[k]:.3g} tol={tol_t[live][k]:.3g}" for k in w))
+    worst = np.max(err[fin_o] / np.maximum(tol[fin_o], 1e-300)) if fin_o.any() else 0.0
+    return int(fin_o.sum()), float(err[fin_o].max() if fin_o.any() else 0.0), float(worst)
+
+
+def test_small_parity_prior_and_ref_particles():
+    binding = require_gpu()
+    r = W.bege_returns()[:120]
+    theta = np.hstack([W.bege_particles(128, seed=6),
+                       W.bege_particles(124, seed=8, centre=W.BEGE_THETA_REF, rel_spread=0.05),
+                       _edge_particles()])
+    out = binding.bege_loglik(torch.from_numpy(theta).cuda(), torch.from_numpy(r).cuda(), H, want_logf=True)
+    ll, logf = to_np(out["ll"]), to_np(out["logf"])
+    n_fin, err, worst = _compare(theta, r, ll, logf)
+    assert n_fin > 100
+    assert np.all(~np.isfinite(ll[-4:]))
+    print(f"BEGE T=120: {n_fin} finite of {theta.shape[1]}, max |dll| {err:.3g}, worst err/tol {worst:.3f}")
+
+
+@pytest.mark.parametrize("n_p,T", [(1, 1), (3, 2), (33, 7), (5, 257)])
+def test_ragged_sizes(n_p, T):
+    binding = require_gpu()
+    r = W.bege_returns(T=T, seed=9)
+    theta = W.bege_particles(n_p, seed=10, centre=W.BEGE_THETA_REF, rel_spread=0.03)
+    out = binding.bege_loglik(torch.from_numpy(theta).cuda(), torch.from_numpy(r).cuda(), H, want_logf=True)
+    _compare(theta, r, to_np(out["ll"]), to_np(out["logf"]))
+
+
+def test_full_size_workload_sampled():
+    """The benchmark's launch (1024 particles x 1099 months); the oracle
+    checks a sample of particles over the whole series."""
+    binding = require_gpu()
+    r = W.bege_returns()
+    theta = W.bege_particles(W.BEGE_N_PARTICLES, seed=6, centre=W.BEGE_THETA_REF, rel_spread=0.05)
+    ll = to_np(binding.bege_loglik(torch.from_numpy(theta).cuda(), torch.from_numpy(r).cuda(), H)["ll"])
+    pick = np.random.default_rng(12).choice(theta.shape[1], 12, replace=False)
+    n_fin, err, worst = _compare(theta[:, pick], r, ll[pick])
+    print(f"BEGE T=1099 sample: {n_fin} finite of {len(pick)}, max |dll| {err:.3g}, worst err/tol {worst:.3f}")
+
+
+def test_invalid_arguments():
+    binding = require_gpu()
+    lib = binding.load_library()
+    th = torch.zeros((11, 4), dtype=torch.float64, device="cuda")
+    r = torch.zeros(8, dtype=torch.float64, device="cuda")
+    ll = torch.empty(4, dtype=torch.float64, device="cuda")
+    ws_bytes = int(lib.bege_loglik_workspace_bytes(4, 8))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    P = binding._ptr
+    assert lib.bege_loglik(P(th), 0, P(r), 8, H, P(ll), None, P(ws), ws_bytes, None) != 0
+    assert lib.bege_loglik(P(th), 4, P(r), 0, H, P(ll), None, P(ws), ws_bytes, None) != 0
+    assert lib.bege_loglik(P(th), 4, P(r), 8, 0.0, P(ll), None, P(ws), ws_bytes, None) != 0
+    assert lib.bege_loglik(P(th), 4, P(r), 8, H, P(ll), None, P(ws), ws_bytes - 1, None) != 0
+    assert lib.bege_loglik(None, 4, P(r), 8, H, P(ll), None, P(ws), ws_bytes, None) != 0
+    assert lib.bege_loglik(P(th), 4, P(r), 8, H, P(ll), None, P(ws), ws_bytes, None) == 0
