@@ -631,9 +631,10 @@ def toggle_mode(args):
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (nominal; not in the measured peaks)
 
 
-def bege_profile(launch_ms):
-    """FP64 operations per bege_density launch from the committed ncu summary
-    (DFMA counted twice), as achieved TFLOP/s; None if absent or stale."""
+def bege_profile(launch_ms, particle_steps):
+    """Executed FP64 operations per particle-step of bege_density from the
+    committed ncu summary (DFMA counted twice), scaled to this launch, as
+    achieved TFLOP/s; None if absent or stale."""
     path = os.path.join(ROOT, "profiles", "bege_density_counts.json")
     try:
         rec = json.load(open(path))
@@ -645,7 +646,7 @@ def bege_profile(launch_ms):
             h.update(f.read())
     if rec.get("source_hash") != h.hexdigest()[:16]:
         return None
-    return rec["fp64_flops_per_launch"] / (launch_ms / 1e3) / 1e12, rec
+    return rec["fp64_flops_per_particle_step"] * particle_steps / (launch_ms / 1e3) / 1e12, rec
 
 
 BEGE_SOURCES = ("paper_1902_09046_gb300/csrc/bege.cu",)
@@ -690,7 +691,7 @@ def bege_mode(args):
             res[name] = {"ms": ms, "particle_steps_per_s": n_p * T / (ms / 1e3),
                          "finite": int(np.isfinite(ll).sum())}
     main = res["later"]
-    prof = bege_profile(main["ms"])
+    prof = bege_profile(main["ms"], n_p * T)
     roof = {"kernel": "bege_density", "bound": "fp64", "unit": "TFLOP/s",
             "peak": FP64_NOMINAL_TFLOPS, "peak_basis": "nominal GB300 dense FP64 (of nominal)",
             "achieved": prof[0] if prof else None, "frac": prof[0] / FP64_NOMINAL_TFLOPS if prof else None,

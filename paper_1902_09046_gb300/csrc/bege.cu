@@ -17,7 +17,9 @@
 // 101 grid nodes spread over the lanes, lgamma of the two shapes computed
 // once per warp, the grid differences taken with shuffles), and a fixed-order
 // reduction of log f over t per particle.  Everything is binary64: the
-// central difference divides the rounding of F by 2h.
+// central difference divides the rounding of F by 2h.  GB300 issues about two
+// binary64 FMAs per SM per clock, so the series avoids divisions: its ratios
+// come from a per-warp table of 1 / (shape + k) in shared memory.
 #include "internal.h"
 
 namespace ppabc {
@@ -48,22 +50,48 @@ struct BegeLayout {
   }
 };
 
-// Regularised lower incomplete gamma P(a, x), a > 0, with lga = lgamma(a):
-// the power series sum_j x^j / (a (a+1) ... (a+j)) times exp(-x + a ln x -
-// lga) for x < a + 1; for x >= a + 1, 1 - Q with Q from Legendre's continued
-// fraction (modified Lentz).  Each loop is bounded by kGammaMaxIter terms.
-__device__ double gammainc_p(double a, double lga, double x) {
+// Reciprocals 1 / (a + k), k < kRecip, of one shape, shared by every node of
+// a task: the series' ratio x / (a + k) becomes x * inv[k] (two roundings
+// instead of one; both well inside the tolerance).
+constexpr int kRecip = 256;
+
+// Nodes with x0 > kTaylorEdge * delta (delta = h / sn) take the central
+// difference of the negative-shock factor from its Taylor expansion, whose
+// relative truncation is about (delta / x0)^4 <= 1e-12; nearer the edge of
+// the support, where the density is not smooth on the scale of delta, both
+// values are evaluated.
+constexpr double kTaylorEdge = 1001.0;
+
+// Where the GPU sums the series (below) rather than the continued fraction.
+constexpr double kSeriesPastShape = 65.0;  // x < a + 1 + 65
+constexpr double kSeriesMaxX = 600.0;      // partial sums stay far below overflow
+
+// Regularised lower incomplete gamma P(a, x), a > 0, with lga = lgamma(a).
+// The power series the paper names,
+//   P = exp(-x + a ln x - lga) sum_j x^j / (a (a+1) ... (a+j)),
+// converges for every x; past x ~ a its terms first grow (to about k = x - a)
+// and then fall, so it needs about (x - a) + sqrt(78 x) terms.  On this GPU a
+// term is two multiplies and an add (table ratios), against about thirty
+// binary64 instructions (two divisions) per step of the continued fraction, so
+// the series is used for every x < a + 1 and, past the shape, for x < a + 66
+// while x < 600 (keeping the growing partial sums far from overflow), and
+// Legendre's continued fraction for Q = 1 - P (modified Lentz) beyond.  Both give P to about 1e-14.  Where the tail bound
+//   Q <= exp(-x + a ln x - lga) / (x + 1 - max(a, 1))     (x > a - 1)
+// is below 2^-56, 1 - Q rounds to 1 whatever Q is, and 1 is returned.  Each
+// loop is bounded by kGammaMaxIter terms.
+__device__ double gammainc_p(double a, double lga, double x, const double* __restrict__ inv) {
   if (!(x > 0.0)) return 0.0;
   const double lead = -x + a * log(x) - lga;
-  if (x < a + 1.0) {
-    double ap = a, term = 1.0 / a, sum = term;
+  const double e = exp(lead);
+  if (x >= a + 1.0 && e < 0x1p-56 * (x + 1.0 - fmax(a, 1.0))) return 1.0;
+  if (x < a + 1.0 || (x < a + 1.0 + kSeriesPastShape && x < kSeriesMaxX)) {
+    double term = inv[0], sum = term;
     for (int k = 1; k < kGammaMaxIter; ++k) {
-      ap += 1.0;
-      term *= x / ap;
+      term *= x * (k < kRecip ? inv[k] : 1.0 / (a + static_cast<double>(k)));
       sum += term;
       if (fabs(term) < fabs(sum) * kGammaEps) break;
     }
-    return sum * exp(lead);
+    return sum * e;
   }
   double b = x + 1.0 - a;
   double c = 1.0 / kGammaTiny;
@@ -81,7 +109,7 @@ __device__ double gammainc_p(double a, double lga, double x) {
     h *= del;
     if (fabs(del - 1.0) < kGammaEps) break;
   }
-  return 1.0 - exp(lead) * h;
+  return 1.0 - e * h;
 }
 
 // Shapes used at each step, one thread per particle; first_bad[i] = the first
@@ -116,13 +144,22 @@ __global__ void bege_shapes(const double* __restrict__ theta, uint32_t np, const
 
 // log f(u_t) for task (i, t) per warp.  Lane l owns grid nodes j = l + 32 k,
 // k = 0..3 (j <= 100): it evaluates P(p, .) at w_j and, for j >= 1, the
-// two P(n, .) at w_{j-1} - (u +- h); the difference P(p, w_j) - P(p, w_{j-1})
-// takes w_{j-1}'s value from the neighbouring lane.
+// central difference over u +- h of the node's factor [1 - P(n, .)]; the
+// difference P(p, w_j) - P(p, w_{j-1}) takes w_{j-1}'s value from the
+// neighbouring lane.  F(u + h) - F(u - h) is accumulated as one sum of
+// per-node differences: the same quantity as the two sums differenced,
+// without their cancellation.  Away from the edge of the negative shock's
+// support the node's difference comes from the Taylor expansion of P(n, .)
+// about the node (one density instead of two series); within kTaylorEdge
+// delta of the edge both values are evaluated.
 __global__ void __launch_bounds__(32 * kBegeWarpsPerCta)
 bege_density(const double* __restrict__ theta, uint32_t np, const double* __restrict__ r, uint32_t T,
              double h, const double* __restrict__ shape_p, const double* __restrict__ shape_n,
              const uint32_t* __restrict__ first_bad, double* __restrict__ logf) {
+  __shared__ double recip[kBegeWarpsPerCta][2][kRecip];
   const uint32_t lane = threadIdx.x & 31u;
+  double* inv_p = recip[threadIdx.x >> 5][0];
+  double* inv_n = recip[threadIdx.x >> 5][1];
   const uint64_t n_tasks = static_cast<uint64_t>(np) * T;
   const uint64_t warp0 = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t n_warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -137,39 +174,54 @@ bege_density(const double* __restrict__ theta, uint32_t np, const double* __rest
     const double lg_own = lgamma(lane == 0 ? p : n);
     const double lgp = __shfl_sync(0xFFFFFFFFu, lg_own, 0);
     const double lgn = __shfl_sync(0xFFFFFFFFu, lg_own, 1);
+    __syncwarp();  // the previous task's readers are done with the tables
+    for (int k = static_cast<int>(lane); k < kRecip; k += 32) {
+      inv_p[k] = 1.0 / (p + static_cast<double>(k));
+      inv_n[k] = 1.0 / (n + static_cast<double>(k));
+    }
+    __syncwarp();
     const double w0 = 1e-4 - p * sp;
     const double dw = (10.0 * sp * sqrt(p) - w0) / static_cast<double>(kBegeNw - 1);
     const double psp = p * sp, nsn = n * sn;
     const double up = u + h, um = u - h;
-    double acc_p = 0.0, acc_m = 0.0;
+    const double delta = h / sn;
+    double acc = 0.0;     // F(u + h) - F(u - h)
     double F_last = 0.0;  // F at node 32 k + 31 of the previous group (lane 31's value)
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int j = static_cast<int>(lane) + 32 * k;
       const bool live = j <= kBegeNw;
       double F = 0.0;
-      if (live) F = gammainc_p(p, lgp, (w0 + static_cast<double>(j) * dw + psp) / sp);
+      if (live) F = gammainc_p(p, lgp, (w0 + static_cast<double>(j) * dw + psp) / sp, inv_p);
       double F_prev = __shfl_up_sync(0xFFFFFFFFu, F, 1);
       if (lane == 0) F_prev = F_last;
       F_last = __shfl_sync(0xFFFFFFFFu, F, 31);
       if (live && j >= 1) {
+        // [1 - P(n, x0 - delta)] - [1 - P(n, x0 + delta)], x0 = (w_{j-1} - u + n sn) / sn.
         const double wjm1 = w0 + static_cast<double>(j - 1) * dw;
-        const double xp = (wjm1 - up + nsn) / sn;
-        const double xm = (wjm1 - um + nsn) / sn;
-        const double Gp = xp > 0.0 ? gammainc_p(n, lgn, xp) : 0.0;
-        const double Gm = xm > 0.0 ? gammainc_p(n, lgn, xm) : 0.0;
-        const double dF = F - F_prev;
-        acc_p += (1.0 - Gp) * dF;
-        acc_m += (1.0 - Gm) * dF;
+        const double x0 = (wjm1 - u + nsn) / sn;
+        double dG;
+        if (x0 > kTaylorEdge * delta) {
+          // P(n, x0 + d) - P(n, x0 - d) = 2 d g + (d^3 / 3) g2 + O(d^5), with the
+          // gamma density g = x^(n-1) e^-x / Gamma(n) and its second derivative
+          // g2 = g [((n-1)/x - 1)^2 - (n-1)/x^2].
+          const double g = exp((n - 1.0) * log(x0) - x0 - lgn);
+          const double q = (n - 1.0) / x0;
+          const double g2 = g * ((q - 1.0) * (q - 1.0) - q / x0);
+          dG = 2.0 * delta * g + (delta * delta * delta / 3.0) * g2;
+        } else {
+          const double xp = (wjm1 - up + nsn) / sn;
+          const double xm = (wjm1 - um + nsn) / sn;
+          dG = (xm > 0.0 ? gammainc_p(n, lgn, xm, inv_n) : 0.0) -
+               (xp > 0.0 ? gammainc_p(n, lgn, xp, inv_n) : 0.0);
+        }
+        acc += dG * (F - F_prev);
       }
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      acc_p += __shfl_xor_sync(0xFFFFFFFFu, acc_p, off);
-      acc_m += __shfl_xor_sync(0xFFFFFFFFu, acc_m, off);
-    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
     if (lane == 0) {
-      const double f = (acc_p - acc_m) / (2.0 * h);
+      const double f = acc / (2.0 * h);
       logf[task] = (f > 0.0 && isfinite(f)) ? log(f) : -INFINITY;
     }
   }

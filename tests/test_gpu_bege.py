@@ -56,26 +56,37 @@ def _shape_sums(theta, r):
     return out
 
 
-def _compare(theta, r, ll_gpu, logf_gpu=None):
+def _compare(theta, r, ll_gpu, logf_gpu):
     ll_o, dens = oracle.bege_loglik(theta, r, H, want_dens=True)
-    fin_o = np.isfinite(ll_o)
-    np.testing.assert_array_equal(np.isfinite(ll_gpu), fin_o)
+    fin_o, fin_g = np.isfinite(ll_o), np.isfinite(ll_gpu)
     s_t = _shape_sums(theta, r)
     with np.errstate(divide="ignore", invalid="ignore"):
-        tol_t = np.where(dens > 0, 1e-13 * (1 + s_t * np.log(2 + s_t)) / (H * dens), 0.0)
-    tol = np.nansum(tol_t, axis=1) + 1e-12 * np.abs(np.where(fin_o, ll_o, 0.0))
+        noise = 1e-13 * (1 + s_t * np.log(2 + s_t)) / H      # absolute rounding scale of f_t
+        tol_t = np.where(dens > 0, noise / dens, 0.0)
+    # A particle may end (-inf) on one side only where the deciding step's
+    # density is within the rounding scale on the other side.
+    for i in np.flatnonzero(fin_o != fin_g):
+        if fin_o[i]:
+            t0 = int(np.flatnonzero(logf_gpu[i] == -np.inf)[0])
+            assert dens[i, t0] <= 2 * noise[i, t0], (i, t0, dens[i, t0], noise[i, t0])
+        else:
+            zero = np.flatnonzero(dens[i] <= 0)
+            assert zero.size, f"particle {i}: the oracle ends it on a shape, the GPU does not"
+            t0 = int(zero[0])
+            assert np.exp(logf_gpu[i, t0]) <= 2 * noise[i, t0], (i, t0, logf_gpu[i, t0], noise[i, t0])
+    both = fin_o & fin_g
+    tol = np.nansum(tol_t, axis=1) + 1e-12 * np.abs(np.where(both, ll_o, 0.0))
     err = np.abs(ll_gpu - ll_o)
-    assert np.all(err[fin_o] <= tol[fin_o]), (err[fin_o].max(), tol[fin_o][np.argmax(err[fin_o])])
-    if logf_gpu is not None:
-        live = dens > 0
-        e = np.abs(logf_gpu[live] - np.log(dens[live]))
-        bad = np.flatnonzero(e > tol_t[live])
-        if bad.size:
-            w = bad[np.argsort(-(e[bad] / tol_t[live][bad]))[:5]]
-            raise AssertionError("per-step log f outside tolerance: " + "; ".join(
-                f"f={dens[live][k]:.4g} s={s_t[live][k]:.4g} err={e[k]:.3g} tol={tol_t[live][k]:.3g}" for k in w))
-    worst = np.max(err[fin_o] / np.maximum(tol[fin_o], 1e-300)) if fin_o.any() else 0.0
-    return int(fin_o.sum()), float(err[fin_o].max() if fin_o.any() else 0.0), float(worst)
+    assert np.all(err[both] <= tol[both]), (err[both].max(), tol[both][np.argmax(err[both])])
+    live = (dens > 0) & np.isfinite(logf_gpu)
+    e = np.abs(logf_gpu[live] - np.log(dens[live]))
+    bad = np.flatnonzero(e > tol_t[live])
+    if bad.size:
+        w = bad[np.argsort(-(e[bad] / tol_t[live][bad]))[:5]]
+        raise AssertionError("per-step log f outside tolerance: " + "; ".join(
+            f"f={dens[live][k]:.4g} s={s_t[live][k]:.4g} err={e[k]:.3g} tol={tol_t[live][k]:.3g}" for k in w))
+    worst = np.max(err[both] / np.maximum(tol[both], 1e-300)) if both.any() else 0.0
+    return int(both.sum()), int((fin_o != fin_g).sum()), float(err[both].max() if both.any() else 0.0), float(worst)
 
 
 def test_small_parity_prior_and_ref_particles():
@@ -86,10 +97,11 @@ def test_small_parity_prior_and_ref_particles():
                        _edge_particles()])
     out = binding.bege_loglik(torch.from_numpy(theta).cuda(), torch.from_numpy(r).cuda(), H, want_logf=True)
     ll, logf = to_np(out["ll"]), to_np(out["logf"])
-    n_fin, err, worst = _compare(theta, r, ll, logf)
-    assert n_fin > 100
+    n_fin, n_edge, err, worst = _compare(theta, r, ll, logf)
+    assert n_fin > 100 and n_edge <= 2
     assert np.all(~np.isfinite(ll[-4:]))
-    print(f"BEGE T=120: {n_fin} finite of {theta.shape[1]}, max |dll| {err:.3g}, worst err/tol {worst:.3f}")
+    print(f"BEGE T=120: {n_fin} finite on both sides of {theta.shape[1]}, {n_edge} ended on one side "
+          f"at a rounding-level density, max |dll| {err:.3g}, worst err/tol {worst:.3f}")
 
 
 @pytest.mark.parametrize("n_p,T", [(1, 1), (3, 2), (33, 7), (5, 257)])
@@ -107,10 +119,12 @@ def test_full_size_workload_sampled():
     binding = require_gpu()
     r = W.bege_returns()
     theta = W.bege_particles(W.BEGE_N_PARTICLES, seed=6, centre=W.BEGE_THETA_REF, rel_spread=0.05)
-    ll = to_np(binding.bege_loglik(torch.from_numpy(theta).cuda(), torch.from_numpy(r).cuda(), H)["ll"])
+    out = binding.bege_loglik(torch.from_numpy(theta).cuda(), torch.from_numpy(r).cuda(), H, want_logf=True)
+    ll, logf = to_np(out["ll"]), to_np(out["logf"])
     pick = np.random.default_rng(12).choice(theta.shape[1], 12, replace=False)
-    n_fin, err, worst = _compare(theta[:, pick], r, ll[pick])
-    print(f"BEGE T=1099 sample: {n_fin} finite of {len(pick)}, max |dll| {err:.3g}, worst err/tol {worst:.3f}")
+    n_fin, n_edge, err, worst = _compare(theta[:, pick], r, ll[pick], logf[pick])
+    print(f"BEGE T=1099 sample: {n_fin} finite of {len(pick)}, {n_edge} edge, max |dll| {err:.3g}, "
+          f"worst err/tol {worst:.3f}")
 
 
 def test_invalid_arguments():
