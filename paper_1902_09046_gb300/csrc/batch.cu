@@ -40,7 +40,7 @@ struct BatchJobDev {
 inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 template <int kThreads>
-__global__ void __launch_bounds__(kThreads) em_ou_batch(const BatchJobDev* __restrict__ jobs,
+__global__ void __launch_bounds__(kThreads, 1152 / kThreads) em_ou_batch(const BatchJobDev* __restrict__ jobs,
                                                         const uint32_t* __restrict__ order,
                                                         uint32_t n_jobs, unsigned int* head,
                                                         unsigned int* cursors) {
@@ -73,7 +73,24 @@ __global__ void __launch_bounds__(kThreads) em_ou_batch(const BatchJobDev* __res
     const BatchJobDev& J = jobs[j];
     const uint32_t n = J.n, spt = J.spt;
     const uint32_t base = tile * (kThreads * spt);
-    for (uint32_t q = 0; q < spt; ++q) {
+    // Samples q and q + 1 of the tile's column run together (ou_path2, the
+    // two-path form of the plain kernel); an odd last one runs alone.
+    uint32_t q = 0;
+    for (; q + 1 < spt; q += 2) {
+      const uint32_t i0 = base + q * kThreads + threadIdx.x;
+      const uint32_t i1 = i0 + kThreads;
+      if (i0 < n) {
+        const uint32_t gi[2] = {i0, i1 < n ? i1 : i0};
+        float th1[2], th2[2], th3[2];
+        ou_prior(J.P, gi[0], th1[0], th2[0], th3[0]);
+        ou_prior(J.P, gi[1], th1[1], th2[1], th3[1]);
+        double d[2];
+        ou_path2<false>(J.P, gi, th1, th2, th3, nullptr, nullptr, 0, d);
+        J.dist[i0] = d[0];
+        if (i1 < n) J.dist[i1] = d[1];
+      }
+    }
+    if (q < spt) {
       const uint32_t i = base + q * kThreads + threadIdx.x;
       if (i < n) {
         float th1, th2, th3;
