@@ -75,7 +75,8 @@ constexpr double kSeriesMaxX = 600.0;      // partial sums stay far below overfl
 // binary64 instructions (two divisions) per step of the continued fraction, so
 // the series is used for every x < a + 1 and, past the shape, for x < a + 66
 // while x < 600 (keeping the growing partial sums far from overflow), and
-// Legendre's continued fraction for Q = 1 - P (modified Lentz) beyond.  Both give P to about 1e-14.  Where the tail bound
+// Legendre's continued fraction for Q = 1 - P (modified Lentz) beyond.  Both
+// give P to about 1e-14.  Where the tail bound
 //   Q <= exp(-x + a ln x - lga) / (x + 1 - max(a, 1))     (x > a - 1)
 // is below 2^-56, 1 - Q rounds to 1 whatever Q is, and 1 is returned.  Each
 // loop is bounded by kGammaMaxIter terms.
@@ -85,11 +86,15 @@ __device__ double gammainc_p(double a, double lga, double x, const double* __res
   const double e = exp(lead);
   if (x >= a + 1.0 && e < 0x1p-56 * (x + 1.0 - fmax(a, 1.0))) return 1.0;
   if (x < a + 1.0 || (x < a + 1.0 + kSeriesPastShape && x < kSeriesMaxX)) {
+    // Two terms per convergence check: at most one extra term, below
+    // kGammaEps of the sum.
     double term = inv[0], sum = term;
-    for (int k = 1; k < kGammaMaxIter; ++k) {
+    for (int k = 1; k < kGammaMaxIter; k += 2) {
       term *= x * (k < kRecip ? inv[k] : 1.0 / (a + static_cast<double>(k)));
       sum += term;
-      if (fabs(term) < fabs(sum) * kGammaEps) break;
+      term *= x * (k + 1 < kRecip ? inv[k + 1] : 1.0 / (a + static_cast<double>(k + 1)));
+      sum += term;
+      if (term < sum * kGammaEps) break;
     }
     return sum * e;
   }
@@ -174,17 +179,30 @@ bege_density(const double* __restrict__ theta, uint32_t np, const double* __rest
     const double lg_own = lgamma(lane == 0 ? p : n);
     const double lgp = __shfl_sync(0xFFFFFFFFu, lg_own, 0);
     const double lgn = __shfl_sync(0xFFFFFFFFu, lg_own, 1);
-    __syncwarp();  // the previous task's readers are done with the tables
-    for (int k = static_cast<int>(lane); k < kRecip; k += 32) {
-      inv_p[k] = 1.0 / (p + static_cast<double>(k));
-      inv_n[k] = 1.0 / (n + static_cast<double>(k));
-    }
-    __syncwarp();
     const double w0 = 1e-4 - p * sp;
     const double dw = (10.0 * sp * sqrt(p) - w0) / static_cast<double>(kBegeNw - 1);
     const double psp = p * sp, nsn = n * sn;
     const double up = u + h, um = u - h;
     const double delta = h / sn;
+    // Each node's decision between the Taylor form and the two values, made
+    // once: the n table is needed only where some node of the warp lies
+    // within kTaylorEdge delta of the negative shock's support edge.
+    bool taylor[4];
+    bool near_edge = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int j = static_cast<int>(lane) + 32 * k;
+      const double x0 = (w0 + static_cast<double>(j - 1) * dw - u + nsn) / sn;
+      taylor[k] = x0 > kTaylorEdge * delta;
+      if (j >= 1 && j <= kBegeNw) near_edge |= !taylor[k];
+    }
+    const bool fill_n = __any_sync(0xFFFFFFFFu, near_edge);
+    __syncwarp();  // the previous task's readers are done with the tables
+    for (int k = static_cast<int>(lane); k < kRecip; k += 32) {
+      inv_p[k] = 1.0 / (p + static_cast<double>(k));
+      if (fill_n) inv_n[k] = 1.0 / (n + static_cast<double>(k));
+    }
+    __syncwarp();
     double acc = 0.0;     // F(u + h) - F(u - h)
     double F_last = 0.0;  // F at node 32 k + 31 of the previous group (lane 31's value)
 #pragma unroll
@@ -201,7 +219,7 @@ bege_density(const double* __restrict__ theta, uint32_t np, const double* __rest
         const double wjm1 = w0 + static_cast<double>(j - 1) * dw;
         const double x0 = (wjm1 - u + nsn) / sn;
         double dG;
-        if (x0 > kTaylorEdge * delta) {
+        if (taylor[k]) {
           // P(n, x0 + d) - P(n, x0 - d) = 2 d g + (d^3 / 3) g2 + O(d^5), with the
           // gamma density g = x^(n-1) e^-x / Gamma(n) and its second derivative
           // g2 = g [((n-1)/x - 1)^2 - (n-1)/x^2].
