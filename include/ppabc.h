@@ -219,8 +219,8 @@ size_t abc_recalibrate_workspace_bytes(uint64_t n, uint64_t k);
  *   N_i  = the k pairs j nearest to summ[:, a] (Euclidean over the n_obs
  *          summaries, binary64 with one fma per coordinate in order; ties to
  *          the smaller index; a itself is one of them),
- *   u_out[d][i] = #{j in N_i : theta[d][j] <= theta[d][a]} / k,
- *   theta_rc_out[d][i] = the ceil(u q)-th smallest (at least the first) of
+ *   u_out[d][i] = c / k with c = #{j in N_i : theta[d][j] <= theta[d][a]},
+ *   theta_rc_out[d][i] = the ceil(c q / k)-th smallest (at least the first) of
  *          theta[d][acc_idx[0..q-1]] -- the u-quantile of the accepted
  *          marginal, i.e. of the posterior given the real observation.
  *   summ     [n_obs][n] double (as abc_prior_predictive's summ_out);

@@ -746,8 +746,10 @@ int orc_recalibrate(const double *summ, const float *theta, uint64_t n, uint32_t
     for (uint64_t i = 0; i < q; ++i) sorted[i] = theta[(uint64_t)d * n + acc[i]];
     qsort(sorted, (size_t)q, sizeof(float), cmp_float_asc);
     for (uint64_t i = 0; i < q; ++i) {
-      double uu = u[(uint64_t)d * q + i];
-      uint64_t r = (uint64_t)ceil(uu * (double)q);
+      /* u = c / k; the rank ceil(u q) = ceil(c q / k) is formed from the count
+       * in integers (the binary64 product u q can round above an integer). */
+      const uint64_t c = (uint64_t)llround(u[(uint64_t)d * q + i] * (double)k);
+      uint64_t r = (c * q + k - 1) / k;
       if (r < 1) r = 1;
       if (r > q) r = q;
       theta_rc[(uint64_t)d * q + i] = sorted[r - 1];

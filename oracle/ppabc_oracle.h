@@ -133,8 +133,9 @@ int orc_toggle_prior_predictive(const orc_toggle_model *m, const double *q_obs, 
  * theta [3][n], acc [q] indices of the accepted pairs.  For accepted i with
  * a = acc[i]: the k pairs nearest to summ[:, a] (Euclidean, ties to the
  * smaller index, a itself included), u[d][i] = #{neighbours j : theta[d][j]
- * <= theta[d][a]} / k, and theta_rc[d][i] = the ceil(u q)-th smallest (at
- * least the first) of theta[d][acc[0..q-1]].  Distances use fma for every
+ * <= theta[d][a]} / k = c / k, and theta_rc[d][i] = the ceil(c q / k)-th
+ * smallest (at least the first) of theta[d][acc[0..q-1]], the rank formed in
+ * integers.  Distances use fma for every
  * squared difference, in summary order. */
 int orc_recalibrate(const double *summ, const float *theta, uint64_t n, uint32_t n_obs,
                     const uint32_t *acc, uint64_t q, uint64_t k, double *u, float *theta_rc,

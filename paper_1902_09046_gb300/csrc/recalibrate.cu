@@ -94,11 +94,11 @@ __global__ void recal_u(const float4* __restrict__ rec_nn, uint32_t k, const flo
   if (threadIdx.x < 3) u_out[static_cast<size_t>(threadIdx.x) * q + i] = static_cast<double>(cnt[threadIdx.x]) / k;
 }
 
-// One CTA per coordinate: sort the accepted marginal, map each u to its
-// ceil(u q)-th smallest value.
+// One CTA per coordinate: sort the accepted marginal, map each u = c / k to
+// its ceil(c q / k)-th smallest value.
 __global__ void __launch_bounds__(1024) recal_quantiles(const float* __restrict__ theta, uint32_t n,
                                                         const uint32_t* __restrict__ acc, uint32_t q,
-                                                        uint32_t P, const double* __restrict__ u,
+                                                        uint32_t k, uint32_t P, const double* __restrict__ u,
                                                         float* __restrict__ theta_rc) {
   extern __shared__ float v[];
   const uint32_t d = blockIdx.x;
@@ -126,9 +126,13 @@ __global__ void __launch_bounds__(1024) recal_quantiles(const float* __restrict_
       theta_rc[static_cast<size_t>(d) * q + i] = __int_as_float(0x7FC00000);
       continue;
     }
-    double r = ceil(ui * static_cast<double>(q));
-    uint32_t ri = r < 1.0 ? 1u : (r > q ? q : static_cast<uint32_t>(r));
-    theta_rc[static_cast<size_t>(d) * q + i] = v[ri - 1];
+    // u = c / k: the rank ceil(u q) = ceil(c q / k) from the count, in
+    // integers (the binary64 product u q can round above an integer).
+    const uint64_t c = static_cast<uint64_t>(llrint(ui * static_cast<double>(k)));
+    uint64_t r = (c * q + k - 1) / k;
+    if (r < 1) r = 1;
+    if (r > q) r = q;
+    theta_rc[static_cast<size_t>(d) * q + i] = v[r - 1];
   }
 }
 
@@ -191,7 +195,7 @@ int abc_recalibrate(const double* summ, const float* theta, uint64_t n, uint32_t
     e = cudaFuncSetAttribute(recal_quantiles, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e == cudaSuccess) {
       recal_quantiles<<<3, 1024, smem, s>>>(theta, static_cast<uint32_t>(n), acc_idx, static_cast<uint32_t>(q),
-                                            Pq, u_out, theta_rc_out);
+                                            static_cast<uint32_t>(k), Pq, u_out, theta_rc_out);
       e = cudaGetLastError();
     }
   }

@@ -315,6 +315,21 @@ def test_recalibration_matches_oracle_on_the_same_pairs():
             assert np.all(to_np(rc["u"]) == 1.0)
 
 
+def test_recalibration_identity_with_every_pair_accepted_and_a_neighbour():
+    """q = n accepted and k = n neighbours: u = rank / n, so every value maps
+    to itself (the rank ceil(u q) formed exactly, not from u q in binary64)."""
+    binding = require_gpu()
+    rng = np.random.default_rng(8)
+    n = 300
+    S = torch.from_numpy(rng.normal(size=(3, n))).cuda()
+    th_np = rng.permutation(np.linspace(0.1, 0.9, 3 * n)).reshape(3, n).astype(np.float32)
+    th = torch.from_numpy(th_np).cuda()
+    acc = torch.arange(n, dtype=torch.int32, device="cuda").to(torch.uint32)
+    rc = binding.abc_recalibrate(S, th, acc, n)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(to_np(rc["theta_rc"]), th_np)
+
+
 def test_recalibration_end_to_end_against_oracle_pairs():
     """GPU pairs against the oracle's own pairs: u agrees to within the few
     neighbours that sit on the k-th distance band."""
