@@ -50,9 +50,9 @@ struct BegeLayout {
   }
 };
 
-// Reciprocals 1 / (a + k), k < kRecip, of one shape, shared by every node of
-// a task: the series' ratio x / (a + k) becomes x * inv[k] (two roundings
-// instead of one; both well inside the tolerance).
+// Reciprocals 1 / (a + k), k < kRecip, of one shape (binary64, stored as
+// double-float), shared by every node of a task: the series' ratio
+// x / (a + k) becomes x * inv[k].
 constexpr int kRecip = 256;
 
 // Nodes with x0 > kTaylorEdge * delta (delta = h / sn) take the central
@@ -61,6 +61,70 @@ constexpr int kRecip = 256;
 // the support, where the density is not smooth on the scale of delta, both
 // values are evaluated.
 constexpr double kTaylorEdge = 1001.0;
+
+// Double-float arithmetic (a value is hi + lo, two binary32 numbers with
+// |lo| <= ulp(hi) / 2; about 48 significant bits): Knuth's two-sum, the
+// FMA two-product and Dekker's normalisation.  GB300 retires about one
+// binary64 FMA per sub-partition every other clock, so a warp-wide binary64
+// instruction holds the pipe about 64 clocks, while the binary32 pipes take
+// a warp instruction per clock: the series below runs in double-float.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return DF{s, b - (s - a)};
+}
+
+__device__ __forceinline__ DF df_split(double x) {
+  const float hi = __double2float_rn(x);
+  return DF{hi, __double2float_rn(x - static_cast<double>(hi))};
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float v = s - a.hi;
+  float e = (a.hi - (s - v)) + (b.hi - v);
+  e += a.lo + b.lo;
+  return df_fast_two_sum(s, e);
+}
+
+// 1 / d for a positive double-float d: the binary32 reciprocal of d.hi and
+// one Newton step r + r (1 - d r), the residual formed in double-float
+// (relative error about 2^-46).
+__device__ __forceinline__ DF df_recip(DF d) {
+  const float r = 1.0f / d.hi;
+  const DF dr = df_mul(d, DF{r, 0.0f});
+  const DF res = df_add(DF{1.0f, 0.0f}, DF{-dr.hi, -dr.lo});
+  return df_fast_two_sum(r, r * res.hi);
+}
+
+// sum_{j>=0} x^j / (a (a+1) ... (a+j)) in double-float, ratios from the
+// table inv[k] = 1 / (a + k) (binary64 beyond it), two terms per
+// convergence check, stopping when a term falls below 2^-49 of the sum (the
+// format's own precision).  All terms are positive; for x < a + 66 they stay
+// below e^66 / a, inside the binary32 range.
+__device__ double series_df(double a, double x, const DF* __restrict__ inv) {
+  const DF xd = df_split(x);
+  DF term = inv[0], sum = term;
+  for (int k = 1; k < kGammaMaxIter; k += 2) {
+    term = df_mul(term, df_mul(xd, k < kRecip ? inv[k] : df_split(1.0 / (a + static_cast<double>(k)))));
+    sum = df_add(sum, term);
+    term = df_mul(term, df_mul(xd, k + 1 < kRecip ? inv[k + 1] : df_split(1.0 / (a + static_cast<double>(k + 1)))));
+    sum = df_add(sum, term);
+    if (term.hi < sum.hi * 0x1p-49f) break;
+  }
+  return static_cast<double>(sum.hi) + static_cast<double>(sum.lo);
+}
 
 // Where the GPU sums the series (below) rather than the continued fraction.
 constexpr double kSeriesPastShape = 65.0;  // x < a + 1 + 65
@@ -80,24 +144,12 @@ constexpr double kSeriesMaxX = 600.0;      // partial sums stay far below overfl
 //   Q <= exp(-x + a ln x - lga) / (x + 1 - max(a, 1))     (x > a - 1)
 // is below 2^-56, 1 - Q rounds to 1 whatever Q is, and 1 is returned.  Each
 // loop is bounded by kGammaMaxIter terms.
-__device__ double gammainc_p(double a, double lga, double x, const double* __restrict__ inv) {
+__device__ double gammainc_p(double a, double lga, double x, const DF* __restrict__ inv) {
   if (!(x > 0.0)) return 0.0;
   const double lead = -x + a * log(x) - lga;
   const double e = exp(lead);
   if (x >= a + 1.0 && e < 0x1p-56 * (x + 1.0 - fmax(a, 1.0))) return 1.0;
-  if (x < a + 1.0 || (x < a + 1.0 + kSeriesPastShape && x < kSeriesMaxX)) {
-    // Two terms per convergence check: at most one extra term, below
-    // kGammaEps of the sum.
-    double term = inv[0], sum = term;
-    for (int k = 1; k < kGammaMaxIter; k += 2) {
-      term *= x * (k < kRecip ? inv[k] : 1.0 / (a + static_cast<double>(k)));
-      sum += term;
-      term *= x * (k + 1 < kRecip ? inv[k + 1] : 1.0 / (a + static_cast<double>(k + 1)));
-      sum += term;
-      if (term < sum * kGammaEps) break;
-    }
-    return sum * e;
-  }
+  if (x < a + 1.0 || (x < a + 1.0 + kSeriesPastShape && x < kSeriesMaxX)) return series_df(a, x, inv) * e;
   double b = x + 1.0 - a;
   double c = 1.0 / kGammaTiny;
   double d = 1.0 / b;
@@ -161,10 +213,10 @@ __global__ void __launch_bounds__(32 * kBegeWarpsPerCta)
 bege_density(const double* __restrict__ theta, uint32_t np, const double* __restrict__ r, uint32_t T,
              double h, const double* __restrict__ shape_p, const double* __restrict__ shape_n,
              const uint32_t* __restrict__ first_bad, double* __restrict__ logf) {
-  __shared__ double recip[kBegeWarpsPerCta][2][kRecip];
+  __shared__ DF recip[kBegeWarpsPerCta][2][kRecip];
   const uint32_t lane = threadIdx.x & 31u;
-  double* inv_p = recip[threadIdx.x >> 5][0];
-  double* inv_n = recip[threadIdx.x >> 5][1];
+  DF* inv_p = recip[threadIdx.x >> 5][0];
+  DF* inv_n = recip[threadIdx.x >> 5][1];
   const uint64_t n_tasks = static_cast<uint64_t>(np) * T;
   const uint64_t warp0 = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t n_warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -183,24 +235,27 @@ bege_density(const double* __restrict__ theta, uint32_t np, const double* __rest
     const double dw = (10.0 * sp * sqrt(p) - w0) / static_cast<double>(kBegeNw - 1);
     const double psp = p * sp, nsn = n * sn;
     const double up = u + h, um = u - h;
-    const double delta = h / sn;
+    const double isp = 1.0 / sp, isn = 1.0 / sn;  // per task: nodes multiply
+    const double delta = h * isn;
     // Each node's decision between the Taylor form and the two values, made
     // once: the n table is needed only where some node of the warp lies
     // within kTaylorEdge delta of the negative shock's support edge.
+    double x0s[4];
     bool taylor[4];
     bool near_edge = false;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int j = static_cast<int>(lane) + 32 * k;
-      const double x0 = (w0 + static_cast<double>(j - 1) * dw - u + nsn) / sn;
-      taylor[k] = x0 > kTaylorEdge * delta;
+      x0s[k] = (w0 + static_cast<double>(j - 1) * dw - u + nsn) * isn;
+      taylor[k] = x0s[k] > kTaylorEdge * delta;
       if (j >= 1 && j <= kBegeNw) near_edge |= !taylor[k];
     }
     const bool fill_n = __any_sync(0xFFFFFFFFu, near_edge);
     __syncwarp();  // the previous task's readers are done with the tables
+    const DF p_df = df_split(p), n_df = df_split(n);
     for (int k = static_cast<int>(lane); k < kRecip; k += 32) {
-      inv_p[k] = 1.0 / (p + static_cast<double>(k));
-      if (fill_n) inv_n[k] = 1.0 / (n + static_cast<double>(k));
+      inv_p[k] = df_recip(df_add(p_df, DF{static_cast<float>(k), 0.0f}));
+      if (fill_n) inv_n[k] = df_recip(df_add(n_df, DF{static_cast<float>(k), 0.0f}));
     }
     __syncwarp();
     double acc = 0.0;     // F(u + h) - F(u - h)
@@ -210,14 +265,14 @@ bege_density(const double* __restrict__ theta, uint32_t np, const double* __rest
       const int j = static_cast<int>(lane) + 32 * k;
       const bool live = j <= kBegeNw;
       double F = 0.0;
-      if (live) F = gammainc_p(p, lgp, (w0 + static_cast<double>(j) * dw + psp) / sp, inv_p);
+      if (live) F = gammainc_p(p, lgp, (w0 + static_cast<double>(j) * dw + psp) * isp, inv_p);
       double F_prev = __shfl_up_sync(0xFFFFFFFFu, F, 1);
       if (lane == 0) F_prev = F_last;
       F_last = __shfl_sync(0xFFFFFFFFu, F, 31);
       if (live && j >= 1) {
         // [1 - P(n, x0 - delta)] - [1 - P(n, x0 + delta)], x0 = (w_{j-1} - u + n sn) / sn.
         const double wjm1 = w0 + static_cast<double>(j - 1) * dw;
-        const double x0 = (wjm1 - u + nsn) / sn;
+        const double x0 = x0s[k];
         double dG;
         if (taylor[k]) {
           // P(n, x0 + d) - P(n, x0 - d) = 2 d g + (d^3 / 3) g2 + O(d^5), with the
@@ -228,8 +283,8 @@ bege_density(const double* __restrict__ theta, uint32_t np, const double* __rest
           const double g2 = g * ((q - 1.0) * (q - 1.0) - q / x0);
           dG = 2.0 * delta * g + (delta * delta * delta / 3.0) * g2;
         } else {
-          const double xp = (wjm1 - up + nsn) / sn;
-          const double xm = (wjm1 - um + nsn) / sn;
+          const double xp = (wjm1 - up + nsn) * isn;
+          const double xm = (wjm1 - um + nsn) * isn;
           dG = (xm > 0.0 ? gammainc_p(n, lgn, xm, inv_n) : 0.0) -
                (xp > 0.0 ? gammainc_p(n, lgn, xp, inv_n) : 0.0);
         }
