@@ -18,7 +18,7 @@ def to_np(t):
     return t.detach().cpu().numpy()
 
 
-# Tolerances, derived in DESIGN.md ("Tolerances"):
+# Tolerances and where they come from:
 #  * a binary32 Box-Muller normal differs from the binary64 one by a few ulp
 #    of the radius: |dz| <= 1e-6 (r <= 5.77, ~3 ulp);
 #  * a binary32 prior draw is within 2 ulp: |dtheta| <= 5e-7 on |theta| <= 2;
