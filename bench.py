@@ -133,10 +133,16 @@ def cpu_baseline(abc, pv, target_s):
     threads = oracle.default_threads()
     frac = calibrate_fraction(abc, pv, threads, target_s)
     steps, dt = run_oracle_sample(abc, pv, frac, threads)
+    # The same oracle on one core, on a sample 1/threads the size (about the
+    # same wall time).
+    frac1 = frac / threads
+    steps1, dt1 = run_oracle_sample(abc, pv, frac1, 1)
     return {"value": steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": (f"first {frac:.3g} of the workload: {int(round(abc.n_samples * frac))} ABC samples "
                        f"x {abc.model['n_steps']} steps + {len(pv.lambdas)} x {int(round(pv.m_sets * frac))} "
-                       f"p-value data sets; FP64, static split over {threads} threads; {dt:.1f} s")}
+                       f"p-value data sets; FP64, static split over {threads} threads; {dt:.1f} s"),
+            "single_core": {"value": steps1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"first {frac1:.3g} of the workload on one thread; {dt1:.1f} s"}}
 
 
 def reference_arm(args):
