@@ -52,7 +52,27 @@ __device__ __forceinline__ float log2_ge1(float x) {
 // of at most p ln2 2^-22 < 1.2e-6, which moves alpha / (1 + x^p) by at most
 // alpha 1.2e-6 / 4 per step; the 0.97 contraction keeps the accumulated
 // effect on u and v below 1e-3 absolute (about 1e-6 of y).
-__device__ __forceinline__ float pow_drift(float x, float p) { return exp2f(p * __log2f(x)); }
+// The hardware approximations are used directly: x >= 1 and p >= 0 keep
+// p log2 x >= 0 and x^p >= 1, so no denormal or overflow handling is needed.
+__device__ __forceinline__ float lg2_hw(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_hw(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float pow_drift(float x, float p) { return ex2_hw(p * lg2_hw(x)); }
+
+// alpha / d for the drift's denominator d = 1 + x^p in [2, 2^126): the
+// hardware reciprocal (relative error about 2^-23) times alpha.
+__device__ __forceinline__ float div_drift(float alpha, float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return alpha * r;
+}
 
 template <bool kWantY, bool kWantSumm, bool kWantTheta>
 __global__ void __launch_bounds__(kTgThreads) toggle_abc(const __grid_constant__ ToggleConst P,
@@ -91,10 +111,10 @@ __global__ void __launch_bounds__(kTgThreads) toggle_abc(const __grid_constant__
         const float zu = h ? z.z : z.x, zv = h ? z.w : z.y;
         const float pu = pow_drift(v, beta_u), pv = pow_drift(u, beta_v);
         float un = 0.97f * u;
-        un += __fdividef(alpha_u, 1.0f + pu) - 1.0f;
+        un += div_drift(alpha_u, 1.0f + pu) - 1.0f;
         un = fmaf(0.5f, zu, un);
         float vn = 0.97f * v;
-        vn += __fdividef(alpha_v, 1.0f + pv) - 1.0f;
+        vn += div_drift(alpha_v, 1.0f + pv) - 1.0f;
         vn = fmaf(0.5f, zv, vn);
         u = fmaxf(un, 1.0f);
         v = fmaxf(vn, 1.0f);
@@ -105,10 +125,10 @@ __global__ void __launch_bounds__(kTgThreads) toggle_abc(const __grid_constant__
     if (j < steps) {  // odd number of steps: one more, eta is lane 2 of this block
       const float pu = pow_drift(v, beta_u), pv = pow_drift(u, beta_v);
       float un = 0.97f * u;
-      un += __fdividef(alpha_u, 1.0f + pu) - 1.0f;
+      un += div_drift(alpha_u, 1.0f + pu) - 1.0f;
       un = fmaf(0.5f, z.x, un);
       float vn = 0.97f * v;
-      vn += __fdividef(alpha_v, 1.0f + pv) - 1.0f;
+      vn += div_drift(alpha_v, 1.0f + pv) - 1.0f;
       vn = fmaf(0.5f, z.y, vn);
       u = fmaxf(un, 1.0f);
       v = fmaxf(vn, 1.0f);
