@@ -527,8 +527,9 @@ int weakinf_test(const double *lambda, uint32_t n_lambda, double lambda0,
  *   w_j = w_0 + j dw,  w_0 = 1e-4 - p sigma_p,  dw = (10 sigma_p sqrt(p) - w_0) / 99,
  * P(a, x) the regularised lower incomplete gamma (0 for x <= 0): its power
  * series for x < a + 1 and Legendre's continued fraction for the complement
- * otherwise.  A scale or shape <= 0, or a density that is not a positive
- * finite number, gives ll_i = -inf.  All arithmetic is binary64.
+ * otherwise.  A scale <= 0, a shape that is not a positive finite number, or
+ * a density that is not a positive finite number, gives ll_i = -inf.  All
+ * arithmetic is binary64.
  *   theta      [11][n_particles] double (device).
  *   r          [T] double (device): the returns r_1..r_T.
  *   h          finite-difference step, 0 < h < 1.

@@ -790,7 +790,7 @@ double orc_gammainc_p(double a, double x) {
       ap += 1.0;
       term *= x / ap;
       sum += term;
-      if (fabs(term) < fabs(sum) * ORC_GAMMA_EPS) break;
+      if (fabs(term) < fabs(sum) * ORC_GAMMA_EPS || term == 0.0) break;
     }
     return sum * exp(lead);
   }
@@ -849,8 +849,9 @@ double orc_bege_density(double u, double sp, double sn, double p, double n, doub
  *   u_t = r_t - mu,  ll = sum_t log f(u_t; sp, sn, p_{t-1}, n_{t-1}),
  * shapes from (p_0, n_0) = (p0, n0) by the printed recursion
  *   p_t = p0 + rho_p p_{t-1} + phi_p^{+|-} / (2 sp^2) u_t^2   (+ if u_t >= 0),
- * and n_t likewise with sn and the n parameters.  A scale or shape <= 0, or a
- * density that is not a positive finite number, gives -inf. */
+ * and n_t likewise with sn and the n parameters.  A scale <= 0, a shape that
+ * is not a positive finite number, or a density that is not a positive finite
+ * number, gives -inf. */
 static double bege_ll_one(const double th[ORC_BEGE_NPAR], const double *r, uint32_t T, double h,
                           double *dens) {
   const double p0 = th[0], sp = th[1], rp = th[2], fpp = th[3], fpm = th[4];
@@ -858,7 +859,7 @@ static double bege_ll_one(const double th[ORC_BEGE_NPAR], const double *r, uint3
   if (!(sp > 0.0) || !(sn > 0.0)) return -INFINITY;
   double p = p0, n = n0, ll = 0.0;
   for (uint32_t t = 0; t < T; ++t) {
-    if (!(p > 0.0) || !(n > 0.0)) return -INFINITY;
+    if (!(p > 0.0) || !(n > 0.0) || !isfinite(p) || !isfinite(n)) return -INFINITY;
     const double u = r[t] - mu;
     const double f = orc_bege_density(u, sp, sn, p, n, h);
     if (dens) dens[t] = f;

@@ -145,9 +145,10 @@ int orc_recalibrate(const double *summ, const float *theta, uint64_t n, uint32_t
  * parameter k of every particle) in the order (p0, sigma_p, rho_p, phi_p+,
  * phi_p-, n0, sigma_n, rho_n, phi_n+, phi_n-, mu); r holds r_1..r_T; the
  * density is the central difference of the discretised distribution function
- * with step h.  ll[np] gets each log-likelihood (-inf where a scale, a shape
- * or a density is not positive); dens[np][T], if non-NULL, the densities
- * (NaN after the step that ended a particle). */
+ * with step h.  ll[np] gets each log-likelihood (-inf where a scale is not
+ * positive, or a shape or a density is not a positive finite number);
+ * dens[np][T], if non-NULL, the densities (NaN after the step that ended a
+ * particle). */
 #define ORC_BEGE_NPAR 11
 #define ORC_BEGE_NW 100
 double orc_gammainc_p(double a, double x);

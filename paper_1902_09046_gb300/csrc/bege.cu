@@ -121,7 +121,7 @@ __device__ double series_df(double a, double x, const DF* __restrict__ inv) {
     sum = df_add(sum, term);
     term = df_mul(term, df_mul(xd, k + 1 < kRecip ? inv[k + 1] : df_split(1.0 / (a + static_cast<double>(k + 1)))));
     sum = df_add(sum, term);
-    if (term.hi < sum.hi * 0x1p-49f) break;
+    if (term.hi < sum.hi * 0x1p-49f || term.hi == 0.0f) break;
   }
   return static_cast<double>(sum.hi) + static_cast<double>(sum.lo);
 }
@@ -170,7 +170,8 @@ __device__ double gammainc_p(double a, double lga, double x, const DF* __restric
 }
 
 // Shapes used at each step, one thread per particle; first_bad[i] = the first
-// step whose scale or shape is not positive (T if none).
+// step whose scale is not positive or whose shape is not a positive finite
+// number (T if none).
 __global__ void bege_shapes(const double* __restrict__ theta, uint32_t np, const double* __restrict__ r,
                             uint32_t T, double* __restrict__ shape_p, double* __restrict__ shape_n,
                             uint32_t* __restrict__ first_bad) {
@@ -185,7 +186,7 @@ __global__ void bege_shapes(const double* __restrict__ theta, uint32_t np, const
   double p = p0, n = n0;
   const double inv2sp2 = 1.0 / (2.0 * sp * sp), inv2sn2 = 1.0 / (2.0 * sn * sn);
   for (uint32_t t = 0; t < T && bad == T; ++t) {
-    if (!(p > 0.0) || !(n > 0.0)) {
+    if (!(p > 0.0) || !(n > 0.0) || !isfinite(p) || !isfinite(n)) {
       bad = t;
       break;
     }

@@ -141,3 +141,14 @@ def test_invalid_particles_are_minus_infinity():
     # discretised distribution function is flat there, f = 0.
     ll, dens = oracle.bege_loglik(_theta(), np.array([0.01, 0.3]), 1e-5, want_dens=True)
     assert ll[0] == -np.inf and dens[0, 1] == 0.0 and dens[0, 0] > 0
+
+
+def test_shape_overflow_is_minus_infinity_and_ends_quickly():
+    """rho > 1 makes the shapes grow without bound; once one is not a finite
+    number the particle ends (-inf) instead of summing a series of zero terms."""
+    import time
+    th = _theta(rp=8.0, rn=8.0)
+    t0 = time.perf_counter()
+    ll = oracle.bege_loglik(th, np.full(400, 0.01), 1e-5)
+    assert ll[0] == -np.inf
+    assert time.perf_counter() - t0 < 20.0
