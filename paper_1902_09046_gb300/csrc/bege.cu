@@ -126,6 +126,67 @@ __device__ double series_df(double a, double x, const DF* __restrict__ inv) {
   return static_cast<double>(sum.hi) + static_cast<double>(sum.lo);
 }
 
+// Binary64 exp and log by Tang's table-driven method (ACM TOMS 15, 1989, and
+// 16, 1990).  Every evaluation of P(a, .) needs exp(-x + a ln x - lgamma(a))
+// and every Taylor node a density, so these two functions are most of the
+// kernel's binary64 work; with the tables they take about ten binary64
+// instructions each.  Accuracy (checked on the CPU with exact FMA): exp within
+// 2.2e-16 relative for x >= -708 (0 below, where the value is < 1e-307 and
+// only ever added to sums of order one), log within 4.2e-16 absolute for
+// positive normal x.
+struct BegeTables {
+  double exp2j[64];   // 2^(j/64)
+  double log_c[128];  // 1 / (1 + j/128), rounded
+  double log_l[128];  // -log(log_c[j])
+};
+
+constexpr double kLn2Over64Hi = 0x1.62e42p-7;  // ln2/64 with 32 trailing zero bits
+constexpr double kLn2Over64Lo = 0x1.fdf473de6af28p-28;
+constexpr double k64OverLn2 = 0x1.71547652b82fep+6;
+constexpr double kLn2Hi = 0x1.62e42p-1;
+constexpr double kLn2Lo = 0x1.fdf473de6af28p-22;
+
+__device__ void bege_fill_tables(BegeTables& tab) {
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) tab.exp2j[i] = exp2(static_cast<double>(i) / 64.0);
+  for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+    const double c = 1.0 / (1.0 + static_cast<double>(i) / 128.0);
+    tab.log_c[i] = c;
+    tab.log_l[i] = -log(c);
+  }
+}
+
+// exp(x) = 2^m 2^(j/64) exp(r), n = 64 m + j = round(64 x / ln2),
+// r = x - n ln2/64 (Cody-Waite, |r| <= ln2/128), exp(r) - 1 to degree 5.
+__device__ __forceinline__ double exp_tab(double x, const BegeTables& tab) {
+  if (!(x >= -708.0)) return x != x ? x : 0.0;
+  if (x > 709.0) return __longlong_as_double(0x7FF0000000000000ll);
+  const double n = rint(x * k64OverLn2);
+  double r = fma(-n, kLn2Over64Hi, x);
+  r = fma(-n, kLn2Over64Lo, r);
+  double p = fma(fma(fma(fma(1.0 / 120.0, r, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5), r, 1.0);
+  p *= r;
+  const int ni = static_cast<int>(n);
+  const double t = tab.exp2j[ni & 63];
+  const double v = fma(t, p, t);
+  return __longlong_as_double(__double_as_longlong(v) + (static_cast<long long>(ni >> 6) << 52));
+}
+
+// log(x) = e ln2 + log(1/c_j) + log1p(r) for x = 2^e m, m in [1, 2), j the
+// top seven bits of m's fraction, r = m c_j - 1 (|r| < 2^-7), log1p to
+// degree 6.  Positive normal x only; anything else takes the library log.
+__device__ __forceinline__ double log_tab(double x, const BegeTables& tab) {
+  if (!(x >= 0x1p-1022) || !(x < __longlong_as_double(0x7FF0000000000000ll))) return log(x);
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int e = static_cast<int>((b >> 52) & 0x7FF) - 1023;
+  const double m = __longlong_as_double(static_cast<long long>((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
+  const int j = static_cast<int>((b >> 45) & 127);
+  const double r = fma(m, tab.log_c[j], -1.0);
+  const double p = fma(fma(fma(fma(fma(-1.0 / 6.0, r, 1.0 / 5.0), r, -0.25), r, 1.0 / 3.0), r, -0.5), r, 1.0);
+  const double q = fma(p, r, tab.log_l[j]);
+  const double ed = static_cast<double>(e);
+  return fma(ed, kLn2Hi, fma(ed, kLn2Lo, q));
+}
+
 // Where the GPU sums the series (below) rather than the continued fraction.
 constexpr double kSeriesPastShape = 65.0;  // x < a + 1 + 65
 constexpr double kSeriesMaxX = 600.0;      // partial sums stay far below overflow
@@ -144,10 +205,10 @@ constexpr double kSeriesMaxX = 600.0;      // partial sums stay far below overfl
 //   Q <= exp(-x + a ln x - lga) / (x + 1 - max(a, 1))     (x > a - 1)
 // is below 2^-56, 1 - Q rounds to 1 whatever Q is, and 1 is returned.  Each
 // loop is bounded by kGammaMaxIter terms.
-__device__ double gammainc_p(double a, double lga, double x, const DF* __restrict__ inv) {
+__device__ double gammainc_p(double a, double lga, double x, const DF* __restrict__ inv, const BegeTables& tab) {
   if (!(x > 0.0)) return 0.0;
-  const double lead = -x + a * log(x) - lga;
-  const double e = exp(lead);
+  const double lead = -x + a * log_tab(x, tab) - lga;
+  const double e = exp_tab(lead, tab);
   if (x >= a + 1.0 && e < 0x1p-56 * (x + 1.0 - fmax(a, 1.0))) return 1.0;
   if (x < a + 1.0 || (x < a + 1.0 + kSeriesPastShape && x < kSeriesMaxX)) return series_df(a, x, inv) * e;
   double b = x + 1.0 - a;
@@ -215,6 +276,9 @@ bege_density(const double* __restrict__ theta, uint32_t np, const double* __rest
              double h, const double* __restrict__ shape_p, const double* __restrict__ shape_n,
              const uint32_t* __restrict__ first_bad, double* __restrict__ logf) {
   __shared__ DF recip[kBegeWarpsPerCta][2][kRecip];
+  __shared__ BegeTables tab;
+  bege_fill_tables(tab);
+  __syncthreads();
   const uint32_t lane = threadIdx.x & 31u;
   DF* inv_p = recip[threadIdx.x >> 5][0];
   DF* inv_n = recip[threadIdx.x >> 5][1];
@@ -266,7 +330,7 @@ bege_density(const double* __restrict__ theta, uint32_t np, const double* __rest
       const int j = static_cast<int>(lane) + 32 * k;
       const bool live = j <= kBegeNw;
       double F = 0.0;
-      if (live) F = gammainc_p(p, lgp, (w0 + static_cast<double>(j) * dw + psp) * isp, inv_p);
+      if (live) F = gammainc_p(p, lgp, (w0 + static_cast<double>(j) * dw + psp) * isp, inv_p, tab);
       double F_prev = __shfl_up_sync(0xFFFFFFFFu, F, 1);
       if (lane == 0) F_prev = F_last;
       F_last = __shfl_sync(0xFFFFFFFFu, F, 31);
@@ -279,15 +343,15 @@ bege_density(const double* __restrict__ theta, uint32_t np, const double* __rest
           // P(n, x0 + d) - P(n, x0 - d) = 2 d g + (d^3 / 3) g2 + O(d^5), with the
           // gamma density g = x^(n-1) e^-x / Gamma(n) and its second derivative
           // g2 = g [((n-1)/x - 1)^2 - (n-1)/x^2].
-          const double g = exp((n - 1.0) * log(x0) - x0 - lgn);
+          const double g = exp_tab((n - 1.0) * log_tab(x0, tab) - x0 - lgn, tab);
           const double q = (n - 1.0) / x0;
           const double g2 = g * ((q - 1.0) * (q - 1.0) - q / x0);
           dG = 2.0 * delta * g + (delta * delta * delta / 3.0) * g2;
         } else {
           const double xp = (wjm1 - up + nsn) * isn;
           const double xm = (wjm1 - um + nsn) * isn;
-          dG = (xm > 0.0 ? gammainc_p(n, lgn, xm, inv_n) : 0.0) -
-               (xp > 0.0 ? gammainc_p(n, lgn, xp, inv_n) : 0.0);
+          dG = (xm > 0.0 ? gammainc_p(n, lgn, xm, inv_n, tab) : 0.0) -
+               (xp > 0.0 ? gammainc_p(n, lgn, xp, inv_n, tab) : 0.0);
         }
         acc += dG * (F - F_prev);
       }
