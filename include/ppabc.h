@@ -57,7 +57,7 @@ extern "C" {
 #define PPABC_EINVAL (-1)     /* invalid argument */
 #define PPABC_ENOMEM (-2)     /* workspace too small / admission refused */
 #define PPABC_ECUDA (-3)      /* a CUDA runtime call or launch failed */
-#define PPABC_ETIMEOUT (-4)   /* a bounded device-side wait expired */
+#define PPABC_ETIMEOUT (-4)   /* a bounded wait expired (ppabc_server_wait) */
 #define PPABC_ENODEV (-5)     /* no sm_103 device current */
 #define PPABC_ECANCELLED (-6) /* job cancelled by the host */
 #define PPABC_PENDING 1       /* server job not finished yet (not an error) */
