@@ -15,8 +15,9 @@
 // are bitonic-sorted there, and the quantiles and distance are formed in
 // binary64.  The state is binary32 (the 0.97 contraction keeps the rounding
 // error of u and v within a few ulp); the drift powers v^beta use the
-// hardware log2 and exp2 (see pow_drift), the observation's u^-gamma an
-// accurate polynomial log2.
+// hardware log2 and exp2 (see toggle_step2), the observation's u^-gamma an
+// accurate polynomial log2.  Each thread runs two cells at once on packed
+// binary32 pairs.
 #include "internal.h"
 
 namespace ppabc {
@@ -47,13 +48,14 @@ __device__ __forceinline__ float log2_ge1(float x) {
   return fmaf(neg2_ln, -0.7213475204444817f, static_cast<float>(e));
 }
 
-// x^p for x >= 1, 0 <= p <= 7, inside the drift alpha / (1 + x^p): the
-// hardware log2 (absolute error about 2^-22) gives x^p to a relative error
-// of at most p ln2 2^-22 < 1.2e-6, which moves alpha / (1 + x^p) by at most
-// alpha 1.2e-6 / 4 per step; the 0.97 contraction keeps the accumulated
-// effect on u and v below 1e-3 absolute (about 1e-6 of y).
-// The hardware approximations are used directly: x >= 1 and p >= 0 keep
-// p log2 x >= 0 and x^p >= 1, so no denormal or overflow handling is needed.
+// The drift x^p (x >= 1, 0 <= p <= 7) is ex2(p lg2(x)) and alpha / (1 + x^p)
+// is alpha times the reciprocal, all three by the hardware approximations
+// used directly: p lg2 x >= 0, x^p >= 1 and 1 + x^p in [2, 2^126), so no
+// denormal or overflow handling is needed.  The log2's absolute error of
+// about 2^-22 gives x^p to a relative error of at most p ln2 2^-22 < 1.2e-6,
+// which moves alpha / (1 + x^p) by at most alpha 1.2e-6 / 4 per step; the
+// 0.97 contraction keeps the accumulated effect on u and v below 1e-3
+// absolute (about 1e-6 of y).
 __device__ __forceinline__ float lg2_hw(float x) {
   float y;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -64,14 +66,33 @@ __device__ __forceinline__ float ex2_hw(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-__device__ __forceinline__ float pow_drift(float x, float p) { return ex2_hw(p * lg2_hw(x)); }
-
-// alpha / d for the drift's denominator d = 1 + x^p in [2, 2^126): the
-// hardware reciprocal (relative error about 2^-23) times alpha.
-__device__ __forceinline__ float div_drift(float alpha, float d) {
+__device__ __forceinline__ float rcp_hw(float d) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
-  return alpha * r;
+  return r;
+}
+
+// One Euler-Maruyama step of both species (Delta t = 1) for two cells at
+// once, lane q = cell q, from the previous (u, v) of each:
+//   u' = max(0.97 u + alpha_u / (1 + v^beta_u) - 1 + 0.5 z_u, 1),
+//   v' = max(0.97 v + alpha_v / (1 + u^beta_v) - 1 + 0.5 z_v, 1),
+// each lane rounded as the one-cell update would be.
+__device__ __forceinline__ void toggle_step2(float2& U, float2& V, float2 zu, float2 zv, float beta_u,
+                                             float beta_v, float alpha_u, float alpha_v) {
+  const float2 eu = mul2(splat2(beta_u), make_float2(lg2_hw(V.x), lg2_hw(V.y)));
+  const float2 ev = mul2(splat2(beta_v), make_float2(lg2_hw(U.x), lg2_hw(U.y)));
+  const float2 du = add2(splat2(1.0f), make_float2(ex2_hw(eu.x), ex2_hw(eu.y)));
+  const float2 dv = add2(splat2(1.0f), make_float2(ex2_hw(ev.x), ex2_hw(ev.y)));
+  const float2 qu = mul2(splat2(alpha_u), make_float2(rcp_hw(du.x), rcp_hw(du.y)));
+  const float2 qv = mul2(splat2(alpha_v), make_float2(rcp_hw(dv.x), rcp_hw(dv.y)));
+  float2 un = mul2(splat2(0.97f), U);
+  un = add2(un, add2(qu, splat2(-1.0f)));
+  un = fma2(splat2(0.5f), zu, un);
+  float2 vn = mul2(splat2(0.97f), V);
+  vn = add2(vn, add2(qv, splat2(-1.0f)));
+  vn = fma2(splat2(0.5f), zv, vn);
+  U = make_float2(fmaxf(un.x, 1.0f), fmaxf(un.y, 1.0f));
+  V = make_float2(fmaxf(vn.x, 1.0f), fmaxf(vn.y, 1.0f));
 }
 
 template <bool kWantY, bool kWantSumm, bool kWantTheta>
@@ -98,47 +119,39 @@ __global__ void __launch_bounds__(kTgThreads) toggle_abc(const __grid_constant__
   const uint32_t T = P.T, C = P.C;
   const uint32_t tag = (P.sub << 8) | kTagTogglePath;
   const uint32_t steps = T - 1;
-  for (uint32_t c = threadIdx.x; c < C; c += kTgThreads) {
-    const PhiloxStream S = philox_stream(P.keys, g, c, tag);
-    float u = 10.0f, v = 10.0f;
+  // Cells c0 and c0 + kTgThreads run together, packed (lane q = cell q): the
+  // same cells per thread as one at a time, with two independent chains.
+  for (uint32_t c0 = threadIdx.x; c0 < C; c0 += 2 * kTgThreads) {
+    const uint32_t c1 = c0 + kTgThreads;
+    const bool has1 = c1 < C;
+    const PhiloxStream S0 = philox_stream(P.keys, g, c0, tag);
+    const PhiloxStream S1 = philox_stream(P.keys, g, has1 ? c1 : c0, tag);
+    float2 U = splat2(10.0f), V = splat2(10.0f);
     // normals 2(j-1), 2(j-1)+1 drive step j: one counter block covers two steps
     uint32_t b = 0;
     uint32_t j = 0;
+    float2 z[4];
     for (; j + 2 <= steps; j += 2, ++b) {
-      const float4 z = normals_of(philox_block(S, P.keys, b));
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float zu = h ? z.z : z.x, zv = h ? z.w : z.y;
-        const float pu = pow_drift(v, beta_u), pv = pow_drift(u, beta_v);
-        float un = 0.97f * u;
-        un += div_drift(alpha_u, 1.0f + pu) - 1.0f;
-        un = fmaf(0.5f, zu, un);
-        float vn = 0.97f * v;
-        vn += div_drift(alpha_v, 1.0f + pv) - 1.0f;
-        vn = fmaf(0.5f, zv, vn);
-        u = fmaxf(un, 1.0f);
-        v = fmaxf(vn, 1.0f);
-      }
+      normals_x2(philox_block(S0, P.keys, b), philox_block(S1, P.keys, b), z);
+      toggle_step2(U, V, z[0], z[1], beta_u, beta_v, alpha_u, alpha_v);
+      toggle_step2(U, V, z[2], z[3], beta_u, beta_v, alpha_u, alpha_v);
     }
-    float eta;
-    const float4 z = normals_of(philox_block(S, P.keys, b));
-    if (j < steps) {  // odd number of steps: one more, eta is lane 2 of this block
-      const float pu = pow_drift(v, beta_u), pv = pow_drift(u, beta_v);
-      float un = 0.97f * u;
-      un += div_drift(alpha_u, 1.0f + pu) - 1.0f;
-      un = fmaf(0.5f, z.x, un);
-      float vn = 0.97f * v;
-      vn += div_drift(alpha_v, 1.0f + pv) - 1.0f;
-      vn = fmaf(0.5f, z.y, vn);
-      u = fmaxf(un, 1.0f);
-      v = fmaxf(vn, 1.0f);
-      eta = z.z;
+    normals_x2(philox_block(S0, P.keys, b), philox_block(S1, P.keys, b), z);
+    float2 eta;
+    if (j < steps) {  // odd number of steps: one more, eta is normal 2 of this block
+      toggle_step2(U, V, z[0], z[1], beta_u, beta_v, alpha_u, alpha_v);
+      eta = z[2];
     } else {
-      eta = z.x;
+      eta = z[0];
     }
-    const float yv = fmaxf(u + mu + mu * sigma * eta * exp2f(-gam * log2_ge1(u)), 1.0f);
-    ys[c] = yv;
-    if (kWantY) y_out[static_cast<size_t>(i) * C + c] = yv;
+    const float y0 = fmaxf(U.x + mu + mu * sigma * eta.x * exp2f(-gam * log2_ge1(U.x)), 1.0f);
+    ys[c0] = y0;
+    if (kWantY) y_out[static_cast<size_t>(i) * C + c0] = y0;
+    if (has1) {
+      const float y1 = fmaxf(U.y + mu + mu * sigma * eta.y * exp2f(-gam * log2_ge1(U.y)), 1.0f);
+      ys[c1] = y1;
+      if (kWantY) y_out[static_cast<size_t>(i) * C + c1] = y1;
+    }
   }
   for (uint32_t c = C + threadIdx.x; c < Ppow2; c += kTgThreads) ys[c] = __int_as_float(0x7F800000);
   __syncthreads();

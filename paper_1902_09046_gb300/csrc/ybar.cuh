@@ -50,23 +50,10 @@ __device__ __forceinline__ double dataset_ybar(const PhiloxKeys& K, double lam, 
 }
 
 // Two data sets at once (lane q = data set q, streams S0 and S1 of the same
-// length): the normals come packed across the sets and the Kahan sums run on
-// packed pairs, with kahan_add's operations in its order (x - y formed as
+// length): the normals come packed across the sets (normals_x2) and the Kahan
+// sums run on packed pairs, with kahan_add's operations in its order (x - y formed as
 // fma(y, -1, x), which rounds identically), so each lane is bit for bit
 // dataset_ybar of its set.
-__device__ __forceinline__ void normals_x2(uint4 w0, uint4 w1, float2 z[4]) {
-  const float2 rA = sqrt_pos2(neg2_log_u01_2(w0.x, w1.x));
-  float2 sA, cA;
-  sincos_2pi_u01_2(w0.y, w1.y, sA, cA);
-  const float2 rB = sqrt_pos2(neg2_log_u01_2(w0.z, w1.z));
-  float2 sB, cB;
-  sincos_2pi_u01_2(w0.w, w1.w, sB, cB);
-  z[0] = mul2(rA, cA);
-  z[1] = mul2(rA, sA);
-  z[2] = mul2(rB, cB);
-  z[3] = mul2(rB, sB);
-}
-
 __device__ __forceinline__ void kahan_add2(float2& s, float2& comp, float2 x) {
   const float2 y = fma2(comp, splat2(-1.0f), x);
   const float2 t = add2(s, y);
