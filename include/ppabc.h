@@ -498,11 +498,14 @@ int toggle_prior_predictive(const ppabc_toggle_model *h_model, const double *h_q
  *   lambda      [n_lambda] double (device).
  *   gamma_out   [n_lambda] double (device).
  *   counts_out  nullable [n_lambda][N] uint32 (device).
+ *   workspace   weakinf_test_workspace_bytes(n_lambda, N) bytes (the |ybar| of
+ *               every data set), 256-byte aligned.
  * Requires 1 <= N <= PPABC_WEAKINF_MAX_SETS, 0 < alpha <= 1, n_obs >= 1.
  */
-int weakinf_test(const double *lambda, uint32_t n_lambda, double lambda0,
-                 uint32_t n_obs, uint64_t n_sets, double alpha, uint64_t seed,
-                 double *gamma_out, uint32_t *counts_out, void *stream);
+size_t weakinf_test_workspace_bytes(uint64_t n_lambda, uint64_t n_sets);
+int weakinf_test(const double *lambda, uint32_t n_lambda, double lambda0, uint32_t n_obs,
+                 uint64_t n_sets, double alpha, uint64_t seed, double *gamma_out,
+                 uint32_t *counts_out, void *workspace, size_t workspace_bytes, void *stream);
 
 /* BEGE likelihood limits and constants. */
 #define PPABC_BEGE_NPAR 11

@@ -39,7 +39,8 @@ EXPORTED = ("ppabc_abi_version", "ppabc_last_error", "ppabc_device_check", "ppab
             "ppabc_batch_plan_destroy", "ppabc_batch_run", "ppabc_server_create",
             "ppabc_server_submit", "ppabc_server_poll", "ppabc_server_wait", "ppabc_server_fetch",
             "ppabc_server_release", "ppabc_server_cancel", "ppabc_server_get_stats",
-            "ppabc_server_now", "ppabc_server_destroy", "weakinf_test", "toggle_prior_predictive",
+            "ppabc_server_now", "ppabc_server_destroy", "weakinf_test_workspace_bytes", "weakinf_test",
+            "toggle_prior_predictive",
             "abc_rejection_workspace_bytes", "abc_rejection", "abc_recalibrate_workspace_bytes",
             "abc_recalibrate", "bege_loglik_workspace_bytes", "bege_loglik")
 WEAKINF_MAX_SETS = 16384
@@ -180,7 +181,8 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
             "ppabc_server_get_stats": ([P, ctypes.POINTER(ServerStats)], i32),
             "ppabc_server_now": ([P], dbl),
             "ppabc_server_destroy": ([P], i32),
-            "weakinf_test": ([P, u32, dbl, u32, u64, dbl, u64, P, P, P], i32),
+            "weakinf_test_workspace_bytes": ([u64, u64], sz),
+            "weakinf_test": ([P, u32, dbl, u32, u64, dbl, u64, P, P, P, sz, P], i32),
             "abc_rejection_workspace_bytes": ([u64], sz),
             "abc_rejection": ([M, P, dbl, u64, u64, u64, u64, u32, P, P, P, P, sz, P], i32),
             "abc_recalibrate_workspace_bytes": ([u64, u64], sz),
@@ -440,9 +442,11 @@ def weakinf_test(lambdas: torch.Tensor, lambda0: float, n_obs: int, n_sets: int,
     gamma = torch.empty(K, dtype=torch.float64, device=lambdas.device)
     counts = (torch.empty((K, n_sets), dtype=torch.uint32, device=lambdas.device)
               if want_counts else None)
-    _check(load_library().weakinf_test(_ptr(lambdas), K, float(lambda0), n_obs, n_sets,
-                                       float(alpha), seed, _ptr(gamma), _ptr(counts),
-                                       _stream(stream)))
+    lib = load_library()
+    ws_bytes = int(lib.weakinf_test_workspace_bytes(K, n_sets))
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=lambdas.device)
+    _check(lib.weakinf_test(_ptr(lambdas), K, float(lambda0), n_obs, n_sets, float(alpha), seed,
+                            _ptr(gamma), _ptr(counts), _ptr(ws), ws_bytes, _stream(stream)))
     return {"gamma": gamma, "counts": counts}
 
 

@@ -58,8 +58,9 @@ cudaError_t launch_toggle(const ToggleConst& P, uint64_t base, uint32_t n, float
                           double* summ_out, float* y_out, double* dist_out, cudaStream_t s);
 
 // Weak-informativity test.
+size_t weakinf_workspace_bytes(uint64_t n_lambda, uint64_t n_sets);
 cudaError_t launch_weakinf(const double* lambda, uint32_t n_lambda, double lambda0, uint32_t n_obs,
                            uint32_t n_sets, double alpha, uint64_t seed, double* gamma_out,
-                           uint32_t* counts_out, cudaStream_t s);
+                           uint32_t* counts_out, void* workspace, cudaStream_t s);
 
 }  // namespace ppabc

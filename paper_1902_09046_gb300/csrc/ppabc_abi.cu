@@ -222,9 +222,13 @@ int pvalue_sweep(const double* lambda, uint32_t n_lambda, uint32_t n_obs, uint64
                     "pvalue_sweep launch");
 }
 
+size_t weakinf_test_workspace_bytes(uint64_t n_lambda, uint64_t n_sets) {
+  return weakinf_workspace_bytes(n_lambda, n_sets);
+}
+
 int weakinf_test(const double* lambda, uint32_t n_lambda, double lambda0, uint32_t n_obs,
                  uint64_t n_sets, double alpha, uint64_t seed, double* gamma_out, uint32_t* counts_out,
-                 void* stream) {
+                 void* workspace, size_t workspace_bytes, void* stream) {
   if (n_lambda == 0) return PPABC_OK;
   if (n_lambda > 0x7FFFFFFFu) return set_error(PPABC_EINVAL, "n_lambda too large");
   if (!lambda || !gamma_out) return set_error(PPABC_EINVAL, "lambda and gamma_out must be non-NULL");
@@ -233,10 +237,14 @@ int weakinf_test(const double* lambda, uint32_t n_lambda, double lambda0, uint32
     return set_error(PPABC_EINVAL, "n_sets must be in [1, %d]", PPABC_WEAKINF_MAX_SETS);
   if (!(alpha > 0.0 && alpha <= 1.0)) return set_error(PPABC_EINVAL, "alpha must be in (0, 1]");
   if (!isfinite(lambda0) || lambda0 < 0.0) return set_error(PPABC_EINVAL, "lambda0 must be >= 0");
+  const size_t need = weakinf_workspace_bytes(n_lambda, n_sets);
+  if (!workspace || workspace_bytes < need)
+    return set_error(PPABC_ENOMEM, "workspace needs %zu bytes, got %zu", need, workspace_bytes);
+  if (reinterpret_cast<uintptr_t>(workspace) & 255u) return set_error(PPABC_EINVAL, "workspace must be 256-byte aligned");
   int rc = require_device();
   if (rc) return rc;
   return check_cuda(launch_weakinf(lambda, n_lambda, lambda0, n_obs, static_cast<uint32_t>(n_sets), alpha,
-                                   seed, gamma_out, counts_out, static_cast<cudaStream_t>(stream)),
+                                   seed, gamma_out, counts_out, workspace, static_cast<cudaStream_t>(stream)),
                     "weakinf launch");
 }
 

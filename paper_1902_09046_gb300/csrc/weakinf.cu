@@ -8,10 +8,13 @@
 // With the sufficient statistic ybar (density falling in |ybar|) the count
 // for base set i is #{j : |ybar_k^j| >= |ybar_0^i|}.
 //
-// One CTA per lambda_k: the N values |ybar_k^j| are drawn into shared memory
-// and bitonic-sorted there, every base set's count is a binary search, and
-// the ceil(alpha N)-th smallest count comes from a shared histogram of the
-// counts.  The paper's N^2 indicator sum becomes N log N work per lambda.
+// Two kernels.  The first draws every |ybar| of both kinds for every lambda
+// over the whole GPU (two data sets per thread, packed as in the p-value
+// sweep) into the caller's workspace.  The second runs one CTA per lambda_k:
+// the N values |ybar_k^j| are bitonic-sorted in shared memory, every base
+// set's count is a binary search, and the ceil(alpha N)-th smallest count
+// comes from a shared histogram of the counts.  The paper's N^2 indicator sum
+// becomes N log N work per lambda.
 #include "internal.h"
 #include "ybar.cuh"
 
@@ -22,19 +25,47 @@ namespace {
 constexpr int kWiThreads = 1024;
 constexpr int kWiMaxPerThread = PPABC_WEAKINF_MAX_SETS / kWiThreads;
 
+// |ybar| of data sets (kind, k, j), kind 0 = lambda_k sets (stream tag PATH,
+// lambda[k]), kind 1 = base sets (tag BASE, lambda0), into abs_out[kind][k][j].
+// Thread t of the grid-stride takes the pair j0 = 2 (t mod ceil(N/2)) and
+// j0 + 1 of one (kind, k).
+__global__ void __launch_bounds__(256) weakinf_ybar(const double* __restrict__ lambda, uint32_t n_lambda,
+                                                    double lambda0, uint32_t n_obs, double inv_n, uint32_t N,
+                                                    const __grid_constant__ PhiloxKeys K,
+                                                    double* __restrict__ abs_out) {
+  const uint32_t half = (N + 1) >> 1;
+  const uint64_t items = 2ull * n_lambda * half;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t t = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < items; t += stride) {
+    const uint32_t jj = static_cast<uint32_t>(t % half);
+    const uint64_t kk = t / half;  // kind * n_lambda + k
+    const uint32_t kind = static_cast<uint32_t>(kk / n_lambda);
+    const uint32_t k = static_cast<uint32_t>(kk % n_lambda);
+    const uint32_t j0 = 2 * jj, j1 = j0 + 1 < N ? j0 + 1 : j0;
+    const double lam = kind ? lambda0 : lambda[k];
+    const double2 yb = dataset_ybar2(K, lam, n_obs, inv_n, j0, j1, k, kind ? kTagBase : kTagPath);
+    double* out = abs_out + (static_cast<size_t>(kind) * n_lambda + k) * N;
+    out[j0] = fabs(yb.x);
+    if (j0 + 1 < N) out[j0 + 1] = fabs(yb.y);
+  }
+}
+
 __global__ void __launch_bounds__(kWiThreads) weakinf_kernel(
-    const double* __restrict__ lambda, double lambda0, uint32_t n_obs, double inv_n, uint32_t N,
-    uint32_t P /* power of two >= N */, uint32_t rank /* ceil(alpha N), 1-based */,
-    const __grid_constant__ PhiloxKeys K, double* __restrict__ gamma_out,
-    uint32_t* __restrict__ counts_out) {
-  extern __shared__ double smem[];  // P doubles; later reused as N+1 histogram bins
+    const double* __restrict__ lam_abs /* [n_lambda][N] */, const double* __restrict__ base_abs,
+    uint32_t N, uint32_t P /* power of two >= N */, uint32_t rank /* ceil(alpha N), 1-based */,
+    double* __restrict__ gamma_out, uint32_t* __restrict__ counts_out) {
+  // The values are |ybar| >= 0 (and +inf padding), whose binary64 bit
+  // patterns order exactly as the numbers: the sort and the searches compare
+  // them as 64-bit integers, on the integer pipes (binary64 compares would
+  // queue on this GPU's narrow FP64 pipe).
+  extern __shared__ unsigned long long smem[];  // P keys; later reused as N+1 histogram bins
   __shared__ unsigned int scan_smem[kWiThreads / 32];
   __shared__ unsigned int s_answer;
   const uint32_t k = blockIdx.x;
-  const double lam = lambda[k];
   // 1. |ybar| of the lambda_k data sets, padded with +inf to P entries.
   for (uint32_t j = threadIdx.x; j < P; j += kWiThreads)
-    smem[j] = j < N ? fabs(dataset_ybar(K, lam, n_obs, inv_n, j, k, kTagPath)) : __longlong_as_double(0x7FF0000000000000ll);
+    smem[j] = j < N ? static_cast<unsigned long long>(__double_as_longlong(lam_abs[static_cast<size_t>(k) * N + j]))
+                    : 0x7FF0000000000000ull;
   __syncthreads();
   // 2. Bitonic sort, ascending.
   for (uint32_t size = 2; size <= P; size <<= 1) {
@@ -43,7 +74,7 @@ __global__ void __launch_bounds__(kWiThreads) weakinf_kernel(
         const uint32_t lo = 2 * t - (t & (stride - 1));
         const uint32_t hi = lo + stride;
         const bool up = (lo & size) == 0;
-        const double a = smem[lo], b = smem[hi];
+        const unsigned long long a = smem[lo], b = smem[hi];
         if ((a > b) == up) {
           smem[lo] = b;
           smem[hi] = a;
@@ -59,7 +90,7 @@ __global__ void __launch_bounds__(kWiThreads) weakinf_kernel(
     const uint32_t i = threadIdx.x + q * kWiThreads;
     my_counts[q] = 0;
     if (i < N) {
-      const double b = fabs(dataset_ybar(K, lambda0, n_obs, inv_n, i, k, kTagBase));
+      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(base_abs[static_cast<size_t>(k) * N + i]));
       uint32_t lo = 0, hi = N;  // search in [0, N)
       while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
@@ -126,9 +157,13 @@ __global__ void __launch_bounds__(kWiThreads) weakinf_kernel(
 
 }  // namespace
 
+size_t weakinf_workspace_bytes(uint64_t n_lambda, uint64_t n_sets) {
+  return 2 * sizeof(double) * n_lambda * n_sets;
+}
+
 cudaError_t launch_weakinf(const double* lambda, uint32_t n_lambda, double lambda0, uint32_t n_obs,
                            uint32_t n_sets, double alpha, uint64_t seed, double* gamma_out,
-                           uint32_t* counts_out, cudaStream_t s) {
+                           uint32_t* counts_out, void* workspace, cudaStream_t s) {
   uint32_t P = 1;
   while (P < n_sets) P <<= 1;
   if (P < 2) P = 2;
@@ -139,9 +174,21 @@ cudaError_t launch_weakinf(const double* lambda, uint32_t n_lambda, double lambd
   uint64_t rank = static_cast<uint64_t>(ceil(alpha * static_cast<double>(n_sets)));
   if (rank < 1) rank = 1;
   if (rank > n_sets) rank = n_sets;
-  weakinf_kernel<<<n_lambda, kWiThreads, smem, s>>>(lambda, lambda0, n_obs, 1.0 / static_cast<double>(n_obs),
-                                                    n_sets, P, static_cast<uint32_t>(rank),
-                                                    philox_keys(seed), gamma_out, counts_out);
+  double* abs_all = static_cast<double*>(workspace);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t items = 2ull * n_lambda * ((n_sets + 1) / 2);
+  uint64_t blocks = (items + 255) / 256;
+  const uint64_t cap = static_cast<uint64_t>(sms > 0 ? sms : 1) * 8 * 4;
+  if (blocks > cap) blocks = cap;
+  weakinf_ybar<<<static_cast<unsigned>(blocks), 256, 0, s>>>(lambda, n_lambda, lambda0, n_obs,
+                                                             1.0 / static_cast<double>(n_obs), n_sets,
+                                                             philox_keys(seed), abs_all);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  weakinf_kernel<<<n_lambda, kWiThreads, smem, s>>>(abs_all, abs_all + static_cast<size_t>(n_lambda) * n_sets,
+                                                    n_sets, P, static_cast<uint32_t>(rank), gamma_out, counts_out);
   return cudaGetLastError();
 }
 
