@@ -7,7 +7,7 @@
 //   counts[k] += [|ybar| >= |ybar_obs|].
 // One thread walks a strided set of data-set pairs of one lambda (blockIdx.y)
 // and keeps its count in a register; a warp reduction and one 64-bit atomic per
-// warp add it to counts[k].  ybar comes from dataset_ybar (binary32 normals,
+// warp add it to counts[k].  ybar comes from dataset_ybar2 (binary32 normals,
 // Kahan-compensated sum, binary64 ybar); the comparison is binary64.
 #include "internal.h"
 #include "ybar.cuh"

@@ -10,50 +10,12 @@
 
 namespace ppabc {
 
-__device__ __forceinline__ void kahan_add(float& s, float& comp, float x) {
-  const float y = x - comp;
-  const float t = s + y;
-  comp = (t - s) - y;
-  s = t;
-}
-
-__device__ __forceinline__ double dataset_ybar(const PhiloxKeys& K, double lam, uint32_t n_obs,
-                                               double inv_n, uint32_t c1, uint32_t c2,
-                                               uint32_t tag) {
-  const PhiloxStream S = philox_stream(K, c1, c2, tag);
-  const uint32_t n_full = (n_obs + 1) >> 2;  // counter blocks whose 4 normals are all used
-  const uint32_t rem = (n_obs + 1) & 3u;     // normals used from the last block
-  float z0 = 0.0f, s = 0.0f, comp = 0.0f;
-  for (uint32_t b = 0; b < n_full; ++b) {
-    const float4 z = normals_of(philox_block(S, K, b));
-    if (b == 0) {
-      z0 = z.x;
-    } else {
-      kahan_add(s, comp, z.x);
-    }
-    kahan_add(s, comp, z.y);
-    kahan_add(s, comp, z.z);
-    kahan_add(s, comp, z.w);
-  }
-  if (rem) {
-    const float4 z = normals_of(philox_block(S, K, n_full));
-    if (n_full == 0) {
-      z0 = z.x;
-    } else {
-      kahan_add(s, comp, z.x);
-    }
-    if (rem > 1) kahan_add(s, comp, z.y);
-    if (rem > 2) kahan_add(s, comp, z.z);
-  }
-  const double sum = static_cast<double>(s) - static_cast<double>(comp);
-  return fma(lam, static_cast<double>(z0), sum * inv_n);
-}
-
 // Two data sets at once (lane q = data set q, streams S0 and S1 of the same
-// length): the normals come packed across the sets (normals_x2) and the Kahan
-// sums run on packed pairs, with kahan_add's operations in its order (x - y formed as
-// fma(y, -1, x), which rounds identically), so each lane is bit for bit
-// dataset_ybar of its set.
+// length): the normals come packed across the sets (normals_x2) and the sums
+// are Kahan-compensated on packed binary32 pairs:
+//   y = x - comp;  t = s + y;  comp = (t - s) - y;  s = t
+// (x - y formed as fma(y, -1, x), which rounds identically), then
+// ybar = lambda z_0 + (s - comp) / n in binary64.
 __device__ __forceinline__ void kahan_add2(float2& s, float2& comp, float2 x) {
   const float2 y = fma2(comp, splat2(-1.0f), x);
   const float2 t = add2(s, y);
