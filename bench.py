@@ -91,7 +91,7 @@ def config_dict(abc, pv, world):
                      f"k={abc.k_accept} + pvalue K={len(pv.lambdas)} M={pv.m_sets} n={pv.n_obs}"),
         "abc_samples_per_rank": abc.n_samples, "em_steps": abc.model["n_steps"],
         "k_accept": abc.k_accept, "pvalue_lambdas": len(pv.lambdas), "pvalue_sets": pv.m_sets,
-        "pvalue_n": pv.n_obs, "sharding": f"sample ranges over {world} rank(s)",
+        "pvalue_n": pv.n_obs, "sharding": f"sample and data-set ranges over {world} rank(s)",
         "l2": "flushed between timed steps (256 MiB write)",
     }
 
@@ -296,6 +296,9 @@ def gpu_arm(args):
     base = rank * N
     if base + N > (1 << 32):
         raise SystemExit("sample range of this rank exceeds 2^32")
+    set_base = rank * pv.m_sets  # each rank draws its own p-value data sets
+    if set_base + pv.m_sets > (1 << 32):
+        raise SystemExit("p-value data-set range of this rank exceeds 2^32")
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
     lam_host = torch.tensor(pv.lambdas, dtype=torch.float64).pin_memory()
@@ -321,8 +324,8 @@ def gpu_arm(args):
             em_events[1].record(stream)
         binding.abc_select(dist_buf, k=abc.k_accept, model=abc.model, seed=abc.seed, sample_base=base,
                            workspace=ws, out=sel_out, stream=stream)
-        binding.pvalue_sweep(lam_dev, pv.n_obs, pv.m_sets, pv.ybar_obs, pv.seed, out=pv_out,
-                             stream=stream)
+        binding.pvalue_sweep(lam_dev, pv.n_obs, pv.m_sets, pv.ybar_obs, pv.seed, set_base=set_base,
+                             out=pv_out, stream=stream)
 
     for _ in range(max(3, args.warmup)):
         step()
