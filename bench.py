@@ -808,6 +808,19 @@ def configs_mode(args):
                  "gpu_path_steps_per_s": res["tried"] * w.model["n_steps"] / (ms / 1e3),
                  "proposals": res["tried"], "accepted": res["n_acc"],
                  "note": "wall time includes the host check of the count every 4 chunks"})
+    # ABC recalibration of the small ABC's accepted sample: its 10^4 stored
+    # pairs, the 100 accepted, 100 neighbours each
+    out = binding.abc_prior_predictive(w.model, w.y_obs, w.n_samples, w.seed, want_theta=True, want_summ=True)
+    sel = binding.abc_select(out["dist"], k=w.k_accept, theta=out["theta"])
+    torch.cuda.synchronize()
+    ms = gpu_ms(lambda: binding.abc_recalibrate(out["summ"], out["theta"], sel["idx"], 100))
+    summ_h, th_h, acc_h = (out["summ"].cpu().numpy(), out["theta"].cpu().numpy(),
+                           sel["idx"].cpu().numpy().astype(np.uint32))
+    t0 = time.perf_counter()
+    oracle.recalibrate(summ_h, th_h, acc_h, 100, n_threads=thr)
+    cpu_s = time.perf_counter() - t0
+    rows.append({"config": "abc_recalibrate_n1e4_q100_k100", "gpu_ms": ms, "oracle_ms": 1e3 * cpu_s,
+                 "oracle_cores": thr, "note": "not a path-step workload: n x q distances and q selections"})
     print(json.dumps({"mode": "configs", "unit": UNIT, "rows": rows}), flush=True)
     return 0
 

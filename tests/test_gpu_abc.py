@@ -344,3 +344,26 @@ def test_recalibration_end_to_end_against_oracle_pairs():
     acc = to_np(sel["idx"]).astype(np.uint32)
     u_o, _ = oracle.recalibrate(s_o.T.copy(), th_o.T.astype(np.float32).copy(), acc, knn)
     assert np.abs(to_np(rc["u"]) - u_o).max() <= 3.0 / knn
+
+
+@pytest.mark.parametrize("n", [300, 24576, 24577])
+def test_recalibration_ties_on_both_sides_of_the_shared_memory_limit(n):
+    """Summaries on a coarse integer grid, so the k-th distance is shared by
+    many pairs: the neighbour set must take the tied pairs in index order on
+    the one-launch path (n up to 24576 keys in shared memory) and on the
+    per-sample selection path above it; u and theta_rc identical to the
+    oracle's."""
+    binding = require_gpu()
+    rng = np.random.default_rng(n)
+    S_np = rng.integers(0, 4, size=(2, n)).astype(np.float64)
+    th_np = rng.random(size=(3, n)).astype(np.float32)
+    acc_np = rng.choice(n, size=7, replace=False).astype(np.uint32)
+    S = torch.from_numpy(S_np).cuda()
+    th = torch.from_numpy(th_np).cuda()
+    acc = torch.from_numpy(acc_np.astype(np.int64)).cuda().to(torch.int32).to(torch.uint32)
+    for k in (1, 37, n // 3, n - 1, n):
+        rc = binding.abc_recalibrate(S, th, acc, k)
+        torch.cuda.synchronize()
+        u_o, rc_o = oracle.recalibrate(S_np, th_np, acc_np, k)
+        np.testing.assert_array_equal(to_np(rc["u"]), u_o)
+        np.testing.assert_array_equal(to_np(rc["theta_rc"]), rc_o)
