@@ -254,7 +254,8 @@ def profiled_traffic(n_samples):
 def pipe_bounds(ms_per_launch, path_steps):
     """The per-pipe ceilings of the kernel from its measured cycles per warp
     step (32 path-steps) on one SM sub-partition -- issue slots, ALU-pipe
-    cycles, FMA-pipe cycles -- read from the committed ncu summary; None if
+    cycles, FMA-pipe cycles, cycles of its heavy sub-pipe -- read from the
+    committed ncu summary; None if
     absent or the kernel changed since.  Each ceiling is the path-step rate if
     that resource alone were busy all the time."""
     path = os.path.join(ROOT, "profiles", "em_ou_fused_traffic.json")
