@@ -638,13 +638,13 @@ def toggle_mode(args):
     return 0
 
 
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (nominal; not in the measured peaks)
 
 
 def bege_profile(launch_ms, particle_steps):
-    """Executed FP64 operations per particle-step of bege_density from the
-    committed ncu summary (DFMA counted twice), scaled to this launch, as
-    achieved TFLOP/s; None if absent or stale."""
+    """Per-pipe ceilings of bege_density from its measured cycles per
+    particle-step on one SM sub-partition (issue slots, FMA pipe and its heavy
+    half, ALU pipe), read from the committed ncu summary, with the achieved
+    rate's fraction of each; None if absent or the kernel changed since."""
     path = os.path.join(ROOT, "profiles", "bege_density_counts.json")
     try:
         rec = json.load(open(path))
@@ -654,12 +654,23 @@ def bege_profile(launch_ms, particle_steps):
     for rel in BEGE_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
-    if rec.get("source_hash") != h.hexdigest()[:16]:
+    cyc = rec.get("cycles_per_particle_step")
+    if rec.get("source_hash") != h.hexdigest()[:16] or not cyc:
         return None
-    return rec["fp64_flops_per_particle_step"] * particle_steps / (launch_ms / 1e3) / 1e12, rec
+    achieved = particle_steps / (launch_ms / 1e3)
+    smsp_cycles_per_s = SM_COUNT * 4 * SM_MAX_MHZ * 1e6
+    out = {"cycles_per_particle_step": cyc}
+    for name, c in cyc.items():
+        if name == "elapsed":
+            continue
+        ceiling = smsp_cycles_per_s / c
+        out[name] = {"ceiling_particle_steps_per_s": ceiling, "frac": achieved / ceiling}
+    out["binding"] = min((k for k in out if k != "cycles_per_particle_step"),
+                         key=lambda k: out[k]["ceiling_particle_steps_per_s"])
+    return out
 
 
-BEGE_SOURCES = ("paper_1902_09046_gb300/csrc/bege.cu",)
+BEGE_SOURCES = ("paper_1902_09046_gb300/csrc/bege.cu", "paper_1902_09046_gb300/csrc/dfloat.cuh")
 
 
 def bege_mode(args):
@@ -702,14 +713,21 @@ def bege_mode(args):
                          "finite": int(np.isfinite(ll).sum())}
     main = res["later"]
     prof = bege_profile(main["ms"], n_p * T)
-    roof = {"kernel": "bege_density", "bound": "fp64", "unit": "TFLOP/s",
-            "peak": FP64_NOMINAL_TFLOPS, "peak_basis": "nominal GB300 dense FP64 (of nominal)",
-            "achieved": prof[0] if prof else None, "frac": prof[0] / FP64_NOMINAL_TFLOPS if prof else None,
-            "traffic": None}
+    if prof:
+        bind = prof[prof["binding"]]
+        roof = {"kernel": "bege_density", "bound": "alu", "unit": "particle-steps/s",
+                "achieved": main["particle_steps_per_s"], "peak": bind["ceiling_particle_steps_per_s"],
+                "frac": bind["frac"], "traffic": None, "pipe_bounds": prof,
+                "peak_basis": (f"{prof['binding']} ceiling: 152 SMs x 4 sub-partitions x 2.07 GHz / "
+                               "measured cycles per particle-step (profiles/bege_density_counts.json)")}
+    else:
+        roof = {"kernel": "bege_density", "bound": "alu", "unit": "particle-steps/s",
+                "achieved": main["particle_steps_per_s"], "peak": None, "frac": None, "traffic": None,
+                "peak_basis": "no current ncu summary for this kernel"}
     line = {"mode": "bege", "metric": "BEGE log-likelihood particle-months/s", "unit": "particle-steps/s",
             "value": main["particle_steps_per_s"], "ms_per_run": main["ms"], "higher_is_better": True,
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "steps": args.steps,
-            "runs": res, "roofline": roof,
+            "vs_baseline": None, "dtype": "f64 sums, double-float (2 x f32) per node", "data": "synthetic (seeded)",
+            "steps": args.steps, "runs": res, "roofline": roof,
             "config": {"workload": f"BEGE log-likelihood, {n_p} particles x T={T} months, N_w=100, h={h:g}; "
                                    "'later' = particles within 5% of the prior box around a plausible "
                                    "vector, 'prior' = prior draws"},

@@ -531,8 +531,12 @@ int weakinf_test(const double *lambda, uint32_t n_lambda, double lambda0, uint32
  * P(a, x) the regularised lower incomplete gamma (0 for x <= 0): its power
  * series for x < a + 1 and Legendre's continued fraction for the complement
  * otherwise.  A scale <= 0, a shape that is not a positive finite number, or
- * a density that is not a positive finite number, gives ll_i = -inf.  All
- * arithmetic is binary64.
+ * a density that is not a positive finite number, gives ll_i = -inf.  The
+ * inputs, shapes and sums over t are binary64; the per-node work (P(a, x),
+ * its prefactor exp(a ln x - x - lgamma(a)), and F(u + h) - F(u - h) taken
+ * node by node, away from the support's edge from the Taylor expansion of
+ * P(n, .) to fifth order in h / sigma_n) runs in double-float (two binary32
+ * numbers, about 48 bits).
  *   theta      [11][n_particles] double (device).
  *   r          [T] double (device): the returns r_1..r_T.
  *   h          finite-difference step, 0 < h < 1.

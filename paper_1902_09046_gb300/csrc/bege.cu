@@ -12,14 +12,23 @@
 //   w_j = w_0 + j dw, w_0 = 1e-4 - p sp, dw = (10 sp sqrt(p) - w_0) / 99.
 //
 // The paper vectorises P(a, x) over a block of V grid nodes on one core.
-// Here three kernels split the work: the shape recursion (sequential in t,
-// one thread per particle), the densities (one warp per (particle, t): the
-// 101 grid nodes spread over the lanes, lgamma of the two shapes computed
-// once per warp, the grid differences taken with shuffles), and a fixed-order
-// reduction of log f over t per particle.  Everything is binary64: the
-// central difference divides the rounding of F by 2h.  GB300 issues about two
-// binary64 FMAs per SM per clock, so the series avoids divisions: its ratios
-// come from a per-warp table of 1 / (shape + k) in shared memory.
+// Here four kernels split the work: the shape recursion (sequential in t,
+// one thread per particle); the per-step constants (one thread per
+// (particle, t): lgamma of both shapes and the node coordinates); the
+// densities (one warp per (particle, t): the 101 grid nodes spread over the
+// lanes, the grid differences taken with shuffles); and log f with a
+// fixed-order sum over t per particle.
+//
+// Precision.  The inputs, the shapes, the node coordinates' constants and the
+// sums over t are binary64.  GB300 retires a binary64 FMA about 32 times
+// slower than a binary32 one, so the per-node work -- the incomplete gamma
+// function (series and continued fraction), the prefactors
+// exp(a ln x - x - lgamma(a)), the gamma densities of the Taylor nodes and
+// the sum over the nodes -- runs in double-float (about 48 bits) on the
+// binary32 pipes.  The prefactor's relative error is about 2^-48 times the
+// size of its exponent (below 1e-11); the binary64 definition itself carries
+// the rounding of F divided by 2h (eps F / h ~ 1e-11 relative).
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace ppabc {
@@ -28,75 +37,43 @@ namespace {
 
 constexpr int kBegeNw = PPABC_BEGE_NW;  // grid intervals
 constexpr int kBegeWarpsPerCta = 8;
-constexpr double kGammaEps = 1e-17;
-constexpr double kGammaTiny = 1e-300;
 constexpr int kGammaMaxIter = 1000000;
 
 inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
-struct BegeLayout {
-  size_t shape_p, shape_n, first_bad, logf, total;
-  BegeLayout(uint64_t np, uint64_t T) {
-    size_t o = 0;
-    shape_p = o;
-    o = align256(o + sizeof(double) * np * T);
-    shape_n = o;
-    o = align256(o + sizeof(double) * np * T);
-    first_bad = o;
-    o = align256(o + sizeof(uint32_t) * np);
-    logf = o;
-    o = align256(o + sizeof(double) * np * T);
-    total = o;
-  }
+// Per-step constants of the density kernel (one record per (particle, t)).
+// Positive-shock node j sits at x_j = xa + j xb (= (w_j + p sp) / sp =
+// (1e-4 + j dw) / sp), negative-shock node j at x0_j = ya + (j - 1) yb
+// (= (w_{j-1} - u + n sn) / sn).
+struct BegeTask {
+  DF xa, xb;    // 1e-4 / sp, dw / sp
+  DF ya, yb;    // (w_0 - u + n sn) / sn, dw / sn
+  DF p, lgp;    // positive shape and lgamma of it
+  DF nm1, lgn;  // negative shape - 1 and lgamma of the shape
+  DF two_delta;  // 2 h / sn
 };
+
 
 // Reciprocals 1 / (a + k), k < kRecip, of one shape (binary64, stored as
 // double-float), shared by every node of a task: the series' ratio
 // x / (a + k) becomes x * inv[k].
 constexpr int kRecip = 256;
 
-// Nodes with x0 > kTaylorEdge * delta (delta = h / sn) take the central
-// difference of the negative-shock factor from its Taylor expansion, whose
-// relative truncation is about (delta / x0)^4 <= 1e-12; nearer the edge of
-// the support, where the density is not smooth on the scale of delta, both
-// values are evaluated.
-constexpr double kTaylorEdge = 1001.0;
-
-// Double-float arithmetic (a value is hi + lo, two binary32 numbers with
-// |lo| <= ulp(hi) / 2; about 48 significant bits): Knuth's two-sum, the
-// FMA two-product and Dekker's normalisation.  GB300 retires about one
-// binary64 FMA per sub-partition every other clock, so a warp-wide binary64
-// instruction holds the pipe about 64 clocks, while the binary32 pipes take
-// a warp instruction per clock: the series below runs in double-float.
-struct DF {
-  float hi, lo;
-};
-
-__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // |a| >= |b|
-  const float s = a + b;
-  return DF{s, b - (s - a)};
-}
-
-__device__ __forceinline__ DF df_split(double x) {
-  const float hi = __double2float_rn(x);
-  return DF{hi, __double2float_rn(x - static_cast<double>(hi))};
-}
-
-__device__ __forceinline__ DF df_mul(DF a, DF b) {
-  const float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  return df_fast_two_sum(p, e);
-}
-
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  const float s = a.hi + b.hi;
-  const float v = s - a.hi;
-  float e = (a.hi - (s - v)) + (b.hi - v);
-  e += a.lo + b.lo;
-  return df_fast_two_sum(s, e);
-}
+// The central difference of the negative-shock factor at node x0 comes from
+// the Taylor expansion of P(n, .) about x0 to fifth order in delta = h / sn,
+//   P(n, x0 + d) - P(n, x0 - d) = 2 d g [1 + (d^2/6) g2/g + (d^4/120) g4/g] + O(d^7 g6),
+// (gk the k-th derivative of the gamma density g) where the node is far from
+// the edge of the support on the scale of delta and ln g varies slowly
+// across it: x0 >= kTaylorEdge delta max(1, |n - 1|) and delta <=
+// kTaylorMaxDelta.  Then delta / x0 <= 0.01 and delta |d ln g / dx| <= 0.03,
+// and the omitted terms are below 1e-12 of the value (checked against the
+// exact difference at 600 digits over shapes 0.05..200); the two corrections,
+// below 2e-4 of the leading term, are formed in binary32 (relative error
+// below 1e-10 of the value).  Elsewhere both values are evaluated (in
+// binary64).
+constexpr float kTaylorEdge = 100.0f;
+enum { kTaylor = 0, kTwoValues = 1, kNone = 2 };
+constexpr float kTaylorMaxDelta = 0.02f;
 
 // 1 / d for a positive double-float d: the binary32 reciprocal of d.hi and
 // one Newton step r + r (1 - d r), the residual formed in double-float
@@ -108,126 +85,148 @@ __device__ __forceinline__ DF df_recip(DF d) {
   return df_fast_two_sum(r, r * res.hi);
 }
 
-// sum_{j>=0} x^j / (a (a+1) ... (a+j)) in double-float, ratios from the
-// table inv[k] = 1 / (a + k) (binary64 beyond it), two terms per
-// convergence check, stopping when a term falls below 2^-49 of the sum (the
-// format's own precision).  All terms are positive; for x < a + 66 they stay
-// below e^66 / a, inside the binary32 range.
-__device__ double series_df(double a, double x, const DF* __restrict__ inv) {
-  const DF xd = df_split(x);
+// sum_{j>=0} x^j / (a (a+1) ... (a+j)), ratios from the table
+// inv[k] = 1 / (a + k) (computed per term beyond it), two terms per
+// convergence check.  Terms at or above 2^-24 of the partial sum are formed and added in
+// double-float; the rest of the tail -- terms that are all below one binary32
+// ulp of the sum -- in binary32, until a term falls below 2^-49 of the sum
+// (the format's own precision).  The binary32 tail's relative error (the
+// rounding of its k products) times its size (below 2^-24 of the sum over
+// 1 - x/(a+k)) stays far below 2^-40 of the sum.  All terms are positive; for
+// x < a + 66 they stay below e^66 / a, inside the binary32 range.
+__device__ DF series_df(DF a_df, DF x, const DF* __restrict__ inv) {
   DF term = inv[0], sum = term;
-  for (int k = 1; k < kGammaMaxIter; k += 2) {
-    term = df_mul(term, df_mul(xd, k < kRecip ? inv[k] : df_split(1.0 / (a + static_cast<double>(k)))));
+  int k = 1;
+  bool small = false;  // the last term is below 2^-24 of the sum
+  for (; k + 1 < kRecip; k += 2) {
+    term = df_mul(term, df_mul(x, inv[k]));
     sum = df_add(sum, term);
-    term = df_mul(term, df_mul(xd, k + 1 < kRecip ? inv[k + 1] : df_split(1.0 / (a + static_cast<double>(k + 1)))));
+    term = df_mul(term, df_mul(x, inv[k + 1]));
     sum = df_add(sum, term);
-    if (term.hi < sum.hi * 0x1p-49f || term.hi == 0.0f) break;
+    if (term.hi < sum.hi * 0x1p-24f) {
+      small = true;
+      k += 2;
+      break;
+    }
   }
-  return static_cast<double>(sum.hi) + static_cast<double>(sum.lo);
+  if (!small) {  // past the table: ratios from binary64
+    for (; k < kGammaMaxIter; k += 2) {
+      term = df_mul(term, df_mul(x, df_recip(df_add_f(a_df, static_cast<float>(k)))));
+      sum = df_add(sum, term);
+      term = df_mul(term, df_mul(x, df_recip(df_add_f(a_df, static_cast<float>(k + 1)))));
+      sum = df_add(sum, term);
+      if (term.hi < sum.hi * 0x1p-24f) {
+        k += 2;
+        break;
+      }
+    }
+  }
+  if (term.hi < sum.hi * 0x1p-49f || term.hi == 0.0f) return sum;
+  const float xf = x.hi, stop = sum.hi * 0x1p-49f;
+  float tf = term.hi, tail = 0.0f;
+  bool done = false;
+  for (; k + 1 < kRecip; k += 2) {
+    tf *= xf * inv[k].hi;
+    tail += tf;
+    tf *= xf * inv[k + 1].hi;
+    tail += tf;
+    if (tf < stop || tf == 0.0f) {
+      done = true;
+      break;
+    }
+  }
+  if (!done) {
+    for (; k < kGammaMaxIter; k += 2) {
+      tf *= xf / (a_df.hi + static_cast<float>(k));
+      tail += tf;
+      tf *= xf / (a_df.hi + static_cast<float>(k + 1));
+      tail += tf;
+      if (tf < stop || tf == 0.0f) break;
+    }
+  }
+  return df_add_f(sum, tail);
 }
 
-// Binary64 exp and log by Tang's table-driven method (ACM TOMS 15, 1989, and
-// 16, 1990).  Every evaluation of P(a, .) needs exp(-x + a ln x - lgamma(a))
-// and every Taylor node a density, so these two functions are most of the
-// kernel's binary64 work; with the tables they take about ten binary64
-// instructions each.  Accuracy (checked on the CPU with exact FMA): exp within
-// 2.2e-16 relative for x >= -708 (0 below, where the value is < 1e-307 and
-// only ever added to sums of order one), log within 4.2e-16 absolute for
-// positive normal x.
-struct BegeTables {
-  double exp2j[64];   // 2^(j/64)
-  double log_c[128];  // 1 / (1 + j/128), rounded
-  double log_l[128];  // -log(log_c[j])
-};
-
-constexpr double kLn2Over64Hi = 0x1.62e42p-7;  // ln2/64 with 32 trailing zero bits
-constexpr double kLn2Over64Lo = 0x1.fdf473de6af28p-28;
-constexpr double k64OverLn2 = 0x1.71547652b82fep+6;
-constexpr double kLn2Hi = 0x1.62e42p-1;
-constexpr double kLn2Lo = 0x1.fdf473de6af28p-22;
-
-__device__ void bege_fill_tables(BegeTables& tab) {
-  for (int i = threadIdx.x; i < 64; i += blockDim.x) tab.exp2j[i] = exp2(static_cast<double>(i) / 64.0);
+// The double-float log and exp tables, computed once per call by one CTA
+// into the workspace (the density kernel's CTAs copy them into shared memory).
+__global__ void __launch_bounds__(128) bege_tables(DfTables* __restrict__ out) {
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) out->exp2j[i] = df_split(exp2(static_cast<double>(i) / 64.0));
   for (int i = threadIdx.x; i < 128; i += blockDim.x) {
-    const double c = 1.0 / (1.0 + static_cast<double>(i) / 128.0);
-    tab.log_c[i] = c;
-    tab.log_l[i] = -log(c);
+    const float c = static_cast<float>(1.0 / (1.0 + (static_cast<double>(i) + 0.5) / 128.0));
+    out->log_c[i] = c;
+    out->log_l[i] = df_split(-log(static_cast<double>(c)));
   }
 }
+static_assert(sizeof(DfTables) % 16 == 0, "the tables are copied as 16-byte words");
 
-// exp(x) = 2^m 2^(j/64) exp(r), n = 64 m + j = round(64 x / ln2),
-// r = x - n ln2/64 (Cody-Waite, |r| <= ln2/128), exp(r) - 1 to degree 5.
-__device__ __forceinline__ double exp_tab(double x, const BegeTables& tab) {
-  if (!(x >= -708.0)) return x != x ? x : 0.0;
-  if (x > 709.0) return __longlong_as_double(0x7FF0000000000000ll);
-  const double n = rint(x * k64OverLn2);
-  double r = fma(-n, kLn2Over64Hi, x);
-  r = fma(-n, kLn2Over64Lo, r);
-  double p = fma(fma(fma(fma(1.0 / 120.0, r, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5), r, 1.0);
-  p *= r;
-  const int ni = static_cast<int>(n);
-  const double t = tab.exp2j[ni & 63];
-  const double v = fma(t, p, t);
-  return __longlong_as_double(__double_as_longlong(v) + (static_cast<long long>(ni >> 6) << 52));
-}
-
-// log(x) = e ln2 + log(1/c_j) + log1p(r) for x = 2^e m, m in [1, 2), j the
-// top seven bits of m's fraction, r = m c_j - 1 (|r| < 2^-7), log1p to
-// degree 6.  Positive normal x only; anything else takes the library log.
-__device__ __forceinline__ double log_tab(double x, const BegeTables& tab) {
-  if (!(x >= 0x1p-1022) || !(x < __longlong_as_double(0x7FF0000000000000ll))) return log(x);
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-  const int e = static_cast<int>((b >> 52) & 0x7FF) - 1023;
-  const double m = __longlong_as_double(static_cast<long long>((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
-  const int j = static_cast<int>((b >> 45) & 127);
-  const double r = fma(m, tab.log_c[j], -1.0);
-  const double p = fma(fma(fma(fma(fma(-1.0 / 6.0, r, 1.0 / 5.0), r, -0.25), r, 1.0 / 3.0), r, -0.5), r, 1.0);
-  const double q = fma(p, r, tab.log_l[j]);
-  const double ed = static_cast<double>(e);
-  return fma(ed, kLn2Hi, fma(ed, kLn2Lo, q));
+// 2^m x for a double-float x with x.hi below 2^100, in at most two exact
+// power-of-two multiplies; results below 2^-126 lose bits or flush to 0
+// (such values of P or of a node's difference enter the sum for f, of order
+// 1e-5 and more, far below its rounding).
+__device__ __forceinline__ DF df_scale(DF x, int m) {
+  if (m < -250) return DF{0.0f, 0.0f};
+  const int m1 = m < -126 ? -126 : m;
+  const float s1 = __int_as_float((m1 + 127) << 23);
+  x = DF{x.hi * s1, x.lo * s1};
+  if (m != m1) {
+    const float s2 = __int_as_float((m - m1 + 127) << 23);
+    x = DF{x.hi * s2, x.lo * s2};
+  }
+  return x;
 }
 
 // Where the GPU sums the series (below) rather than the continued fraction.
-constexpr double kSeriesPastShape = 65.0;  // x < a + 1 + 65
-constexpr double kSeriesMaxX = 600.0;      // partial sums stay far below overflow
+constexpr float kSeriesPastShape = 65.0f;  // x < a + 1 + 65
+constexpr float kCfTiny = 1e-30f;           // modified Lentz's floor for d and c
 
-// Regularised lower incomplete gamma P(a, x), a > 0, with lga = lgamma(a).
+// Regularised lower incomplete gamma P(a, x), a > 0, given a, lgamma(a) and x
+// as double-floats (af = a rounded to binary32), in double-float throughout.
 // The power series the paper names,
-//   P = exp(-x + a ln x - lga) sum_j x^j / (a (a+1) ... (a+j)),
-// converges for every x; past x ~ a its terms first grow (to about k = x - a)
-// and then fall, so it needs about (x - a) + sqrt(78 x) terms.  On this GPU a
-// term is two multiplies and an add (table ratios), against about thirty
-// binary64 instructions (two divisions) per step of the continued fraction, so
-// the series is used for every x < a + 1 and, past the shape, for x < a + 66
-// while x < 600 (keeping the growing partial sums far from overflow), and
-// Legendre's continued fraction for Q = 1 - P (modified Lentz) beyond.  Both
-// give P to about 1e-14.  Where the tail bound
-//   Q <= exp(-x + a ln x - lga) / (x + 1 - max(a, 1))     (x > a - 1)
-// is below 2^-56, 1 - Q rounds to 1 whatever Q is, and 1 is returned.  Each
-// loop is bounded by kGammaMaxIter terms.
-__device__ double gammainc_p(double a, double lga, double x, const DF* __restrict__ inv, const BegeTables& tab) {
-  if (!(x > 0.0)) return 0.0;
-  const double lead = -x + a * log_tab(x, tab) - lga;
-  const double e = exp_tab(lead, tab);
-  if (x >= a + 1.0 && e < 0x1p-56 * (x + 1.0 - fmax(a, 1.0))) return 1.0;
-  if (x < a + 1.0 || (x < a + 1.0 + kSeriesPastShape && x < kSeriesMaxX)) return series_df(a, x, inv) * e;
-  double b = x + 1.0 - a;
-  double c = 1.0 / kGammaTiny;
-  double d = 1.0 / b;
-  double h = d;
-  for (int i = 1; i < kGammaMaxIter; ++i) {
-    const double an = -i * (i - a);
-    b += 2.0;
-    d = fma(an, d, b);
-    if (fabs(d) < kGammaTiny) d = kGammaTiny;
-    c = b + an / c;
-    if (fabs(c) < kGammaTiny) c = kGammaTiny;
-    d = 1.0 / d;
-    const double del = d * c;
-    h *= del;
-    if (fabs(del - 1.0) < kGammaEps) break;
+//   P = exp(-x + a ln x - lgamma(a)) sum_j x^j / (a (a+1) ... (a+j)),
+// converges for every x; past x ~ a its terms first grow (to about k = x - a,
+// the largest about e^((x-a)^2 / 2a) / x, inside the binary32 range for
+// x < a + 66) and then fall, so it needs about (x - a) + sqrt(78 x) terms.
+// The series is used for every x < a + 1 and, past the shape, for
+// x < a + 66; beyond, Legendre's continued fraction for Q = 1 - P (modified
+// Lentz), which converges in a few terms there.  Where the tail bound
+//   Q <= exp(-x + a ln x - lgamma(a)) / (x + 1 - max(a, 1))     (x > a - 1)
+// is below 2^-56, 1 - Q rounds to 1 whatever Q is, and 1 is returned.  The
+// branches are decided on binary32 copies of x and a.  Each loop is bounded
+// by kGammaMaxIter terms.
+__device__ DF gammainc_p_df(float af, DF a_df, DF lga, DF x, const DF* __restrict__ inv, const DfTables& dtab) {
+  if (!(x.hi > 0.0f)) return DF{0.0f, 0.0f};
+  const DF lead = df_add(df_mul(a_df, df_log(x, dtab)), df_neg(df_add(x, lga)));  // a ln x - x - lgamma(a)
+  const float xf = x.hi;
+  const bool upper = xf >= af + 1.0f;
+  // Tail bound exp(lead) / (x + 1 - max(a, 1)) < 2^-56, in the log domain.
+  if (upper && lead.hi < -38.816242f + __logf(xf + 1.0f - fmaxf(af, 1.0f))) return DF{1.0f, 0.0f};
+  if (lead.hi < -700.0f) return DF{upper ? 1.0f : 0.0f, 0.0f};  // P < 1e-270 or 1 - P < 1e-270
+  int m;
+  const DF v = df_exp_scaled(lead, m, dtab);  // exp(lead) = 2^m v, v in [1, 2)
+  if (!upper || xf < af + 1.0f + kSeriesPastShape) {
+    // series x v: the series is at least 1/a and below e^66 / a, so the
+    // product is a normal binary32 pair before the scaling.
+    return df_scale(df_mul(series_df(a_df, x, inv), v), m);
   }
-  return 1.0 - e * h;
+  // Q = exp(lead) / (x + 1 - a - 1 (1 - a) / (x + 3 - a - 2 (2 - a) / (x + 5 - a - ...))).
+  DF b = df_add(df_add_f(x, 1.0f), df_neg(a_df));
+  DF c = DF{1.0f / kCfTiny, 0.0f};
+  DF d = df_recip(b);
+  DF hq = d;
+  for (int i = 1; i < kGammaMaxIter; ++i) {
+    const DF an = df_mul_f(df_add_f(df_neg(a_df), static_cast<float>(i)), -static_cast<float>(i));  // -i (i - a)
+    b = df_add_f(b, 2.0f);
+    d = df_add(df_mul(an, d), b);
+    if (fabsf(d.hi) < kCfTiny) d = DF{kCfTiny, 0.0f};
+    c = df_add(b, df_mul(an, df_recip(c)));
+    if (fabsf(c.hi) < kCfTiny) c = DF{kCfTiny, 0.0f};
+    d = df_recip(d);
+    const DF del = df_mul(d, c);
+    hq = df_mul(hq, del);
+    if (fabsf(df_add_f(del, -1.0f).hi) < 0x1p-47f) break;
+  }
+  const DF q = df_scale(df_mul(hq, v), m);
+  return df_add_f(df_neg(q), 1.0f);
 }
 
 // Shapes used at each step, one thread per particle; first_bad[i] = the first
@@ -261,23 +260,62 @@ __global__ void bege_shapes(const double* __restrict__ theta, uint32_t np, const
   first_bad[i] = bad;
 }
 
-// log f(u_t) for task (i, t) per warp.  Lane l owns grid nodes j = l + 32 k,
-// k = 0..3 (j <= 100): it evaluates P(p, .) at w_j and, for j >= 1, the
+// Per-step constants, one thread per (particle, t): lgamma of both shapes
+// and the node coordinates' offsets and spacings, as double-floats.  The
+// density kernel runs one warp per (particle, t); doing this binary64 work
+// there would run it on a whole warp for one set of values.
+__global__ void __launch_bounds__(256) bege_tasks(const double* __restrict__ theta, uint32_t np,
+                                                  const double* __restrict__ r, uint32_t T, double h,
+                                                  const double* __restrict__ shape_p,
+                                                  const double* __restrict__ shape_n,
+                                                  const uint32_t* __restrict__ first_bad, uint64_t n_tasks,
+                                                  BegeTask* __restrict__ tasks) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t task = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; task < n_tasks;
+       task += stride) {
+    const uint32_t i = static_cast<uint32_t>(task / T);
+    const uint32_t t = static_cast<uint32_t>(task % T);
+    if (t >= first_bad[i]) continue;
+    const double sp = theta[np + i], sn = theta[6ull * np + i], mu = theta[10ull * np + i];
+    const double p = shape_p[task], n = shape_n[task];
+    const double u = r[t] - mu;
+    const double w0 = 1e-4 - p * sp;
+    const double dw = (10.0 * sp * sqrt(p) - w0) / static_cast<double>(kBegeNw - 1);
+    BegeTask k;
+    k.xa = df_split(1e-4 / sp);
+    k.xb = df_split(dw / sp);
+    k.ya = df_split((w0 - u + n * sn) / sn);
+    k.yb = df_split(dw / sn);
+    k.p = df_split(p);
+    k.lgp = df_split(lgamma(p));
+    k.nm1 = df_split(n - 1.0);
+    k.lgn = df_split(lgamma(n));
+    k.two_delta = df_split(2.0 * h / sn);
+    tasks[task] = k;
+  }
+}
+
+// f(u_t) for task (i, t) per warp.  Lane l owns grid nodes j = l + 32 k,
+// k = 0..3 (j <= 100): it evaluates P(p, .) at x_j and, for j >= 1, the
 // central difference over u +- h of the node's factor [1 - P(n, .)]; the
-// difference P(p, w_j) - P(p, w_{j-1}) takes w_{j-1}'s value from the
+// difference P(p, x_j) - P(p, x_{j-1}) takes x_{j-1}'s value from the
 // neighbouring lane.  F(u + h) - F(u - h) is accumulated as one sum of
 // per-node differences: the same quantity as the two sums differenced,
 // without their cancellation.  Away from the edge of the negative shock's
 // support the node's difference comes from the Taylor expansion of P(n, .)
-// about the node (one density instead of two series); within kTaylorEdge
-// delta of the edge both values are evaluated.
-__global__ void __launch_bounds__(32 * kBegeWarpsPerCta)
-bege_density(const double* __restrict__ theta, uint32_t np, const double* __restrict__ r, uint32_t T,
-             double h, const double* __restrict__ shape_p, const double* __restrict__ shape_n,
-             const uint32_t* __restrict__ first_bad, double* __restrict__ logf) {
+// about the node (one density instead of two series); near the edge both
+// values are evaluated.  f is written to fout (bege_finish takes its log).
+__global__ void __launch_bounds__(32 * kBegeWarpsPerCta, 3)
+bege_density(uint32_t np, uint32_t T, double inv_2h, const DfTables* __restrict__ tables,
+             const BegeTask* __restrict__ tasks,
+             const uint32_t* __restrict__ first_bad, double* __restrict__ fout) {
   __shared__ DF recip[kBegeWarpsPerCta][2][kRecip];
-  __shared__ BegeTables tab;
-  bege_fill_tables(tab);
+  __shared__ DfTables dtab;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(tables);
+    uint4* dst = reinterpret_cast<uint4*>(&dtab);
+    for (uint32_t q = threadIdx.x; q < sizeof(DfTables) / sizeof(uint4); q += blockDim.x) dst[q] = src[q];
+  }
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31u;
   DF* inv_p = recip[threadIdx.x >> 5][0];
@@ -289,103 +327,142 @@ bege_density(const double* __restrict__ theta, uint32_t np, const double* __rest
     const uint32_t i = static_cast<uint32_t>(task / T);
     const uint32_t t = static_cast<uint32_t>(task % T);
     if (t >= first_bad[i]) continue;  // the whole warp skips together
-    const double sp = theta[np + i], sn = theta[6ull * np + i], mu = theta[10ull * np + i];
-    const double p = shape_p[task], n = shape_n[task];
-    const double u = r[t] - mu;
-    // lgamma of the two shapes, once per warp.
-    const double lg_own = lgamma(lane == 0 ? p : n);
-    const double lgp = __shfl_sync(0xFFFFFFFFu, lg_own, 0);
-    const double lgn = __shfl_sync(0xFFFFFFFFu, lg_own, 1);
-    const double w0 = 1e-4 - p * sp;
-    const double dw = (10.0 * sp * sqrt(p) - w0) / static_cast<double>(kBegeNw - 1);
-    const double psp = p * sp, nsn = n * sn;
-    const double up = u + h, um = u - h;
-    const double isp = 1.0 / sp, isn = 1.0 / sn;  // per task: nodes multiply
-    const double delta = h * isn;
+    const BegeTask K = tasks[task];
+    const float delta_f = 0.5f * K.two_delta.hi;
+    const float pf = K.p.hi;
     // Each node's decision between the Taylor form and the two values, made
-    // once: the n table is needed only where some node of the warp lies
-    // within kTaylorEdge delta of the negative shock's support edge.
-    double x0s[4];
-    bool taylor[4];
+    // once: the n table is needed only where some node of the warp is not a
+    // Taylor node.
+    DF x0s[4];
+    int kind[4];  // kTaylor, kTwoValues or kNone (both values below 1e-297)
     bool near_edge = false;
+    const float nf = K.nm1.hi + 1.0f, lgn_f = K.lgn.hi;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int j = static_cast<int>(lane) + 32 * k;
-      x0s[k] = (w0 + static_cast<double>(j - 1) * dw - u + nsn) * isn;
-      taylor[k] = x0s[k] > kTaylorEdge * delta;
-      if (j >= 1 && j <= kBegeNw) near_edge |= !taylor[k];
+      x0s[k] = df_add(K.ya, df_mul_f(K.yb, static_cast<float>(j - 1)));
+      const float xm = x0s[k].hi + delta_f;
+      if (delta_f <= kTaylorMaxDelta && x0s[k].hi >= kTaylorEdge * delta_f * fmaxf(1.0f, fabsf(K.nm1.hi))) {
+        kind[k] = kTaylor;
+      } else if (!(xm > 0.0f) || (xm < nf && nf * __logf(xm) - xm - lgn_f < -700.0f)) {
+        // P(n, x) <= e^(n ln x - x - lgamma(n)) (n + 1) / n for x < n: both
+        // values are below 1e-297 (and no table is needed).
+        kind[k] = kNone;
+      } else {
+        kind[k] = kTwoValues;
+        if (j >= 1 && j <= kBegeNw) near_edge = true;
+      }
     }
     const bool fill_n = __any_sync(0xFFFFFFFFu, near_edge);
+    const DF n_df = df_add_f(K.nm1, 1.0f);
     __syncwarp();  // the previous task's readers are done with the tables
-    const DF p_df = df_split(p), n_df = df_split(n);
     for (int k = static_cast<int>(lane); k < kRecip; k += 32) {
-      inv_p[k] = df_recip(df_add(p_df, DF{static_cast<float>(k), 0.0f}));
+      inv_p[k] = df_recip(df_add(K.p, DF{static_cast<float>(k), 0.0f}));
       if (fill_n) inv_n[k] = df_recip(df_add(n_df, DF{static_cast<float>(k), 0.0f}));
     }
     __syncwarp();
-    double acc = 0.0;     // F(u + h) - F(u - h)
-    double F_last = 0.0;  // F at node 32 k + 31 of the previous group (lane 31's value)
+    DF acc = DF{0.0f, 0.0f};     // F(u + h) - F(u - h): a sum of non-negative terms
+    DF F_last = DF{0.0f, 0.0f};  // F at node 32 k + 31 of the previous group (lane 31's value)
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int j = static_cast<int>(lane) + 32 * k;
       const bool live = j <= kBegeNw;
-      double F = 0.0;
-      if (live) F = gammainc_p(p, lgp, (w0 + static_cast<double>(j) * dw + psp) * isp, inv_p, tab);
-      double F_prev = __shfl_up_sync(0xFFFFFFFFu, F, 1);
+      DF F = DF{0.0f, 0.0f};
+      if (live) F = gammainc_p_df(pf, K.p, K.lgp, df_add(K.xa, df_mul_f(K.xb, static_cast<float>(j))), inv_p, dtab);
+      DF F_prev = DF{__shfl_up_sync(0xFFFFFFFFu, F.hi, 1), __shfl_up_sync(0xFFFFFFFFu, F.lo, 1)};
       if (lane == 0) F_prev = F_last;
-      F_last = __shfl_sync(0xFFFFFFFFu, F, 31);
+      F_last = DF{__shfl_sync(0xFFFFFFFFu, F.hi, 31), __shfl_sync(0xFFFFFFFFu, F.lo, 31)};
       if (live && j >= 1) {
         // [1 - P(n, x0 - delta)] - [1 - P(n, x0 + delta)], x0 = (w_{j-1} - u + n sn) / sn.
-        const double wjm1 = w0 + static_cast<double>(j - 1) * dw;
-        const double x0 = x0s[k];
-        double dG;
-        if (taylor[k]) {
-          // P(n, x0 + d) - P(n, x0 - d) = 2 d g + (d^3 / 3) g2 + O(d^5), with the
-          // gamma density g = x^(n-1) e^-x / Gamma(n) and its second derivative
-          // g2 = g [((n-1)/x - 1)^2 - (n-1)/x^2].
-          const double g = exp_tab((n - 1.0) * log_tab(x0, tab) - x0 - lgn, tab);
-          const double q = (n - 1.0) / x0;
-          const double g2 = g * ((q - 1.0) * (q - 1.0) - q / x0);
-          dG = 2.0 * delta * g + (delta * delta * delta / 3.0) * g2;
+        const DF x0 = x0s[k];
+        DF dG;
+        if (kind[k] == kTaylor) {
+          // Gamma density g = x^(n-1) e^-x / Gamma(n).  With the derivatives of
+          // ln g, L1 = (n-1)/x - 1, L2 = -(n-1)/x^2, L3 = 2(n-1)/x^3 and
+          // L4 = -6(n-1)/x^4: g2/g = L1^2 + L2 and
+          // g4/g = L1^4 + 6 L1^2 L2 + 4 L1 L3 + 3 L2^2 + L4.
+          const DF arg = df_add(df_mul(K.nm1, df_log(x0, dtab)), df_neg(df_add(x0, K.lgn)));
+          if (arg.hi < -700.0f) {
+            dG = DF{0.0f, 0.0f};
+          } else {
+            int m;
+            const DF g = df_exp_scaled(arg, m, dtab);  // g = 2^m (hi + lo)
+            const float ix = 1.0f / x0.hi;
+            const float q = K.nm1.hi * ix;
+            const float L1 = q - 1.0f, L2 = -q * ix;
+            const float L3 = -2.0f * L2 * ix, L4 = -3.0f * L3 * ix;
+            const float d2 = delta_f * delta_f;
+            const float c2 = (d2 / 6.0f) * fmaf(L1, L1, L2);
+            const float c4 = (d2 * d2 / 120.0f) *
+                             (L1 * L1 * (L1 * L1 + 6.0f * L2) + 4.0f * L1 * L3 + 3.0f * L2 * L2 + L4);
+            dG = df_scale(df_mul(g, df_add_f(K.two_delta, K.two_delta.hi * (c2 + c4))), m);
+          }
+        } else if (kind[k] == kNone) {
+          dG = DF{0.0f, 0.0f};
         } else {
-          const double xp = (wjm1 - up + nsn) * isn;
-          const double xm = (wjm1 - um + nsn) * isn;
-          dG = (xm > 0.0 ? gammainc_p(n, lgn, xm, inv_n, tab) : 0.0) -
-               (xp > 0.0 ? gammainc_p(n, lgn, xp, inv_n, tab) : 0.0);
+          // Both values in double-float.  Their relative difference is at
+          // least about 2 delta |d ln g / dx| > 0.02 here (the node failed the
+          // Taylor test), so the difference keeps about 42 bits; where x0 - d
+          // is outside the support it is P(n, x0 + d) itself.
+          const DF half_delta = DF{0.5f * K.two_delta.hi, 0.5f * K.two_delta.lo};
+          const DF xm = df_add(x0, half_delta), xp = df_add(x0, df_neg(half_delta));
+          const DF Pm = gammainc_p_df(nf, n_df, K.lgn, xm, inv_n, dtab);
+          dG = xp.hi > 0.0f ? df_add(Pm, df_neg(gammainc_p_df(nf, n_df, K.lgn, xp, inv_n, dtab))) : Pm;
         }
-        acc += dG * (F - F_prev);
+        acc = df_add(acc, df_mul(dG, df_add(F, df_neg(F_prev))));
       }
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
-    if (lane == 0) {
-      const double f = acc / (2.0 * h);
-      logf[task] = (f > 0.0 && isfinite(f)) ? log(f) : -INFINITY;
-    }
+    for (int off = 16; off > 0; off >>= 1)
+      acc = df_add(acc, DF{__shfl_xor_sync(0xFFFFFFFFu, acc.hi, off), __shfl_xor_sync(0xFFFFFFFFu, acc.lo, off)});
+    if (lane == 0) fout[task] = df_to_double(acc) * inv_2h;
   }
 }
 
-// ll_i = sum_{t < T} log f, fixed-order tree per particle; -inf if a step
-// was invalid or a density was not positive.
-__global__ void __launch_bounds__(256) bege_reduce(const double* __restrict__ logf, uint32_t T,
+// log f per step (in place: f -> log f, -inf where f is not a positive
+// finite number) and ll_i = sum_{t < T} log f in a fixed-order tree per
+// particle; -inf if a step was invalid or a density was not positive.
+__global__ void __launch_bounds__(256) bege_finish(double* __restrict__ logf, uint32_t T,
                                                    const uint32_t* __restrict__ first_bad,
                                                    double* __restrict__ ll) {
   __shared__ double part[256];
   const uint32_t i = blockIdx.x;
-  if (first_bad[i] < T) {
-    if (threadIdx.x == 0) ll[i] = -INFINITY;
-    return;
-  }
+  const uint32_t t_end = first_bad[i] < T ? first_bad[i] : T;
   double s = 0.0;
-  for (uint32_t t = threadIdx.x; t < T; t += 256) s += logf[static_cast<size_t>(i) * T + t];
+  for (uint32_t t = threadIdx.x; t < t_end; t += 256) {
+    const double f = logf[static_cast<size_t>(i) * T + t];
+    const double lf = (f > 0.0 && isfinite(f)) ? log(f) : -INFINITY;
+    logf[static_cast<size_t>(i) * T + t] = lf;
+    s += lf;
+  }
   part[threadIdx.x] = s;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < static_cast<unsigned>(w)) part[threadIdx.x] += part[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) ll[i] = part[0] != part[0] ? -INFINITY : part[0];
+  if (threadIdx.x == 0) ll[i] = (first_bad[i] < T || part[0] != part[0]) ? -INFINITY : part[0];
 }
+
+struct BegeLayout {
+  size_t shape_p, shape_n, tasks, tables, first_bad, logf, total;
+  BegeLayout(uint64_t np, uint64_t T) {
+    size_t o = 0;
+    shape_p = o;
+    o = align256(o + sizeof(double) * np * T);
+    shape_n = o;
+    o = align256(o + sizeof(double) * np * T);
+    tasks = o;
+    o = align256(o + sizeof(BegeTask) * np * T);
+    tables = o;
+    o = align256(o + sizeof(DfTables));
+    first_bad = o;
+    o = align256(o + sizeof(uint32_t) * np);
+    logf = o;
+    o = align256(o + sizeof(double) * np * T);
+    total = o;
+  }
+};
 
 }  // namespace
 
@@ -416,6 +493,8 @@ int bege_loglik(const double* theta, uint64_t n_particles, const double* r, uint
   char* w = static_cast<char*>(workspace);
   double* shape_p = reinterpret_cast<double*>(w + L.shape_p);
   double* shape_n = reinterpret_cast<double*>(w + L.shape_n);
+  BegeTask* tasks = reinterpret_cast<BegeTask*>(w + L.tasks);
+  DfTables* tables = reinterpret_cast<DfTables*>(w + L.tables);
   uint32_t* first_bad = reinterpret_cast<uint32_t*>(w + L.first_bad);
   double* logf = logf_out ? logf_out : reinterpret_cast<double*>(w + L.logf);
   const uint32_t np = static_cast<uint32_t>(n_particles);
@@ -425,24 +504,34 @@ int bege_loglik(const double* theta, uint64_t n_particles, const double* r, uint
     e = cudaMemsetAsync(logf_out, 0xFF, sizeof(double) * n_particles * T, s);
   }
   if (e == cudaSuccess) {
+    bege_tables<<<1, 128, 0, s>>>(tables);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
     bege_shapes<<<(np + 127) / 128, 128, 0, s>>>(theta, np, r, T, shape_p, shape_n, first_bad);
     e = cudaGetLastError();
   }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t n_tasks = n_particles * T;
   if (e == cudaSuccess) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint64_t tasks = n_particles * T;
-    const uint64_t per_cta = kBegeWarpsPerCta;
-    uint64_t blocks = (tasks + per_cta - 1) / per_cta;
-    const uint64_t cap = static_cast<uint64_t>(sms > 0 ? sms : 1) * 64;
-    if (blocks > cap) blocks = cap;
-    bege_density<<<static_cast<unsigned>(blocks), 32 * kBegeWarpsPerCta, 0, s>>>(
-        theta, np, r, T, h, shape_p, shape_n, first_bad, logf);
+    const uint64_t want = (n_tasks + 255) / 256, cap = static_cast<uint64_t>(sms > 0 ? sms : 1) * 8;
+    bege_tasks<<<static_cast<unsigned>(want < cap ? want : cap), 256, 0, s>>>(theta, np, r, T, h, shape_p, shape_n,
+                                                                                first_bad, n_tasks, tasks);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    bege_reduce<<<np, 256, 0, s>>>(logf, T, first_bad, ll_out);
+    const uint64_t per_cta = kBegeWarpsPerCta;
+    uint64_t blocks = (n_tasks + per_cta - 1) / per_cta;
+    const uint64_t cap = static_cast<uint64_t>(sms > 0 ? sms : 1) * 64;
+    if (blocks > cap) blocks = cap;
+    bege_density<<<static_cast<unsigned>(blocks), 32 * kBegeWarpsPerCta, 0, s>>>(np, T, 0.5 / h, tables, tasks,
+                                                                                 first_bad, logf);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    bege_finish<<<np, 256, 0, s>>>(logf, T, first_bad, ll_out);
     e = cudaGetLastError();
   }
   return check_cuda(e, "bege_loglik");

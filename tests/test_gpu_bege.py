@@ -1,11 +1,13 @@
-"""GPU parity of the BEGE log-likelihood (C ABI vs CPU oracle, both binary64).
+"""GPU parity of the BEGE log-likelihood (C ABI vs the binary64 CPU oracle).
 
-Tolerance: each side forms F(u +- h) as a sum of 100 products of incomplete
-gamma values.  Those carry the rounding of their exponent -x + a ln x -
-lnGamma(a), which the two sides evaluate with different libraries: about
+Tolerance: the oracle forms F(u +- h) as two sums of 100 products of
+incomplete gamma values and divides their difference by 2h (h = 1e-5).  Each
+value carries the rounding of its exponent -x + a ln x - lnGamma(a): about
 eps (x + a |ln x| + |lnGamma(a)|) relative, i.e. ~1e-15 for shapes near 1 and
-~1e-13 for shapes in the hundreds.  The central difference divides by 2h
-(h = 1e-5).  So step t allows
+~1e-13 for shapes in the hundreds, and the difference divides that by h.  The
+GPU takes the difference node by node (no cancellation) and evaluates the
+per-node work in double-float (48 bits): its own error, about 2^-48 times the
+same exponent size, is far inside the oracle's.  So step t allows
   |d log f_t| <= 1e-13 (1 + s_t ln(2 + s_t)) / (h f_t),  s_t = p_{t-1} + n_{t-1},
 with f_t from the oracle, and a particle the sum of that plus 1e-12 |ll|."""
 import numpy as np
