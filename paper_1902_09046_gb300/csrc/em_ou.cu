@@ -6,22 +6,11 @@
 // This replaces the paper's block-of-VECL SIMD loop with pre-generated
 // normals (Sec. 3.4): on the GPU a warp is the SIMD vector, the sample index
 // is the lane, and the normals never touch memory.
-#include <stdlib.h>
-
 #include "internal.h"
 
 namespace ppabc {
 
 constexpr int kEmThreads = 128;
-
-// PPABC_EM_PAIRS=0 selects the one-sample-per-thread kernel (for comparison).
-bool em_pairs_enabled() {
-  static const bool on = [] {
-    const char* v = getenv("PPABC_EM_PAIRS");
-    return !(v && v[0] == '0');
-  }();
-  return on;
-}
 
 template <bool kWantTheta, bool kWantSumm>
 __global__ void __launch_bounds__(kEmThreads) em_ou_fused(const __grid_constant__ OUConst P,
@@ -64,7 +53,7 @@ __global__ void __launch_bounds__(kEmThreads, 10) em_ou_fused_x2(const __grid_co
 cudaError_t launch_em_ou(const OUConst& P, uint64_t base, uint32_t n, float* theta_out,
                          double* summ_out, double* dist_out, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  if (!theta_out && !summ_out && em_pairs_enabled()) {
+  if (!theta_out && !summ_out) {
     const dim3 grid2((n + 2 * kEmThreads - 1) / (2 * kEmThreads));
     em_ou_fused_x2<<<grid2, kEmThreads, 0, s>>>(P, static_cast<uint32_t>(base), n, dist_out);
     return cudaGetLastError();
