@@ -7,6 +7,7 @@ library with the CUDA runtime linked statically.  The output lives in
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -48,10 +49,22 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    if not force and not extra_flags and up_to_date():
-        return LIB_PATH
-    nvcc = _nvcc()
+    """Builds the library unless it is up to date.  Processes that build at
+    once (the ranks of one node) take turns on a lock file, so the later ones
+    find the library built."""
     os.makedirs(OUT_DIR, exist_ok=True)
+    with open(os.path.join(OUT_DIR, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and not extra_flags and up_to_date():
+                return LIB_PATH
+            return _build_locked(verbose, extra_flags)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose: bool, extra_flags: list[str] | None) -> str:
+    nvcc = _nvcc()
     flags = NVCC_FLAGS + list(extra_flags or [])
 
     def compile_one(src: str) -> str:
