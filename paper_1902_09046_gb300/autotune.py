@@ -19,7 +19,7 @@ import torch
 
 from . import binding
 
-CANDIDATES = ((128, 1024), (128, 4096), (128, 16384), (256, 4096))
+CANDIDATES = ((128, 1024), (128, 4096), (128, 16384))
 
 
 def _cache_path() -> str:
