@@ -50,6 +50,96 @@ __global__ void __launch_bounds__(256) weakinf_ybar(const double* __restrict__ l
   }
 }
 
+// Register-blocked bitonic sort of kWiRegKeys = 16 * kWiThreads keys (one
+// lambda's padded sets when N > 8192): thread t holds the run 16 t .. 16 t +
+// 15 in registers.  Merges whose stride is below 16 stay inside a run and run
+// in registers; the wider ones go through shared memory, where element e of
+// run t sits at 16 t + 2 ((e / 2 mod 8) xor (t mod 8)) + e mod 2, so that
+// the runs' 16-byte chunks, read and written a chunk per lane, spread over
+// all banks.  55 shared-memory stages and barriers instead of 105.
+constexpr uint32_t kWiRegKeys = 16u * kWiThreads;
+
+__device__ __forceinline__ uint32_t wi_phys(uint32_t e) {
+  return (e & ~15u) | (((((e >> 1) & 7u) ^ ((e >> 4) & 7u))) << 1) | (e & 1u);
+}
+
+__device__ __forceinline__ void wi_cas(unsigned long long& a, unsigned long long& b, bool up) {
+  const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
+  a = up ? lo : hi;
+  b = up ? hi : lo;
+}
+
+// In-register stages of one merge size, strides `first` .. 1 (first <= 8).
+__device__ __forceinline__ void wi_reg_stages(unsigned long long (&r)[16], uint32_t t, uint32_t size,
+                                              uint32_t first) {
+#pragma unroll
+  for (uint32_t st = 8; st > 0; st >>= 1) {
+    if (st > first) continue;
+#pragma unroll
+    for (uint32_t i = 0; i < 16; ++i) {
+      if (i & st) continue;
+      wi_cas(r[i], r[i + st], ((16u * t + i) & size) == 0u);
+    }
+  }
+}
+
+__device__ __forceinline__ void wi_store_run(unsigned long long* smem, const unsigned long long (&r)[16],
+                                             uint32_t t) {
+#pragma unroll
+  for (uint32_t c = 0; c < 8; ++c) {
+    ulonglong2 v;
+    v.x = r[2 * c];
+    v.y = r[2 * c + 1];
+    *reinterpret_cast<ulonglong2*>(smem + 16u * t + 2u * (c ^ (t & 7u))) = v;
+  }
+}
+
+__device__ __forceinline__ void wi_load_run(const unsigned long long* smem, unsigned long long (&r)[16],
+                                            uint32_t t) {
+#pragma unroll
+  for (uint32_t c = 0; c < 8; ++c) {
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(smem + 16u * t + 2u * (c ^ (t & 7u)));
+    r[2 * c] = v.x;
+    r[2 * c + 1] = v.y;
+  }
+}
+
+// Sorts the kWiRegKeys keys src[0..N) (+inf beyond) ascending into smem, in
+// the layout wi_phys describes.
+__device__ void wi_sort_blocked(const double* __restrict__ src, uint32_t N, unsigned long long* smem) {
+  const uint32_t t = threadIdx.x;
+  unsigned long long r[16];
+#pragma unroll
+  for (uint32_t i = 0; i < 16; ++i) {
+    const uint32_t e = 16u * t + i;
+    r[i] = e < N ? static_cast<unsigned long long>(__double_as_longlong(src[e])) : 0x7FF0000000000000ull;
+  }
+#pragma unroll
+  for (uint32_t size = 2; size <= 16; size <<= 1) wi_reg_stages(r, t, size, size >> 1);
+  for (uint32_t size = 32; size <= kWiRegKeys; size <<= 1) {
+    wi_store_run(smem, r, t);
+    __syncthreads();
+    for (uint32_t stride = size >> 1; stride >= 16; stride >>= 1) {
+#pragma unroll
+      for (uint32_t u = 0; u < kWiRegKeys / 2 / kWiThreads; ++u) {
+        const uint32_t tt = t + u * kWiThreads;
+        const uint32_t lo = 2 * tt - (tt & (stride - 1));
+        const uint32_t plo = wi_phys(lo), phi = wi_phys(lo + stride);
+        unsigned long long a = smem[plo], b = smem[phi];
+        if ((a > b) == ((lo & size) == 0)) {
+          smem[plo] = b;
+          smem[phi] = a;
+        }
+      }
+      __syncthreads();
+    }
+    wi_load_run(smem, r, t);
+    wi_reg_stages(r, t, size, 8);
+  }
+  wi_store_run(smem, r, t);
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kWiThreads) weakinf_kernel(
     const double* __restrict__ lam_abs /* [n_lambda][N] */, const double* __restrict__ base_abs,
     uint32_t N, uint32_t P /* power of two >= N */, uint32_t rank /* ceil(alpha N), 1-based */,
@@ -58,30 +148,43 @@ __global__ void __launch_bounds__(kWiThreads) weakinf_kernel(
   // patterns order exactly as the numbers: the sort and the searches compare
   // them as 64-bit integers, on the integer pipes (binary64 compares would
   // queue on this GPU's narrow FP64 pipe).
-  extern __shared__ unsigned long long smem[];  // P keys; later reused as N+1 histogram bins
+  extern __shared__ __align__(16) unsigned long long smem[];  // P keys; later reused as N+1 histogram bins
   __shared__ unsigned int scan_smem[kWiThreads / 32];
   __shared__ unsigned int s_answer;
   const uint32_t k = blockIdx.x;
-  // 1. |ybar| of the lambda_k data sets, padded with +inf to P entries.
-  for (uint32_t j = threadIdx.x; j < P; j += kWiThreads)
-    smem[j] = j < N ? static_cast<unsigned long long>(__double_as_longlong(lam_abs[static_cast<size_t>(k) * N + j]))
-                    : 0x7FF0000000000000ull;
-  __syncthreads();
-  // 2. Bitonic sort, ascending.
-  for (uint32_t size = 2; size <= P; size <<= 1) {
-    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-      for (uint32_t t = threadIdx.x; t < (P >> 1); t += kWiThreads) {
-        const uint32_t lo = 2 * t - (t & (stride - 1));
-        const uint32_t hi = lo + stride;
-        const bool up = (lo & size) == 0;
-        const unsigned long long a = smem[lo], b = smem[hi];
-        if ((a > b) == up) {
-          smem[lo] = b;
-          smem[hi] = a;
+  const bool blocked = P == kWiRegKeys;  // the register-blocked sort and its layout
+  if (blocked) {
+    wi_sort_blocked(lam_abs + static_cast<size_t>(k) * N, N, smem);
+  } else {
+    // 1. |ybar| of the lambda_k data sets, padded with +inf to P entries.
+    for (uint32_t j = threadIdx.x; j < P; j += kWiThreads)
+      smem[j] = j < N ? static_cast<unsigned long long>(__double_as_longlong(lam_abs[static_cast<size_t>(k) * N + j]))
+                      : 0x7FF0000000000000ull;
+    __syncthreads();
+    // 2. Bitonic sort, ascending.  At a stride of at most 32 the pairs of warp
+    // w's thread t (t = 32 w + lane + 1024 m) lie in the 64-element block
+    // starting at 64 (w + 32 m), the same block at every such stride, so
+    // between two such stages only the warp has to synchronise.
+    for (uint32_t size = 2; size <= P; size <<= 1) {
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t t = threadIdx.x; t < (P >> 1); t += kWiThreads) {
+          const uint32_t lo = 2 * t - (t & (stride - 1));
+          const uint32_t hi = lo + stride;
+          const bool up = (lo & size) == 0;
+          const unsigned long long a = smem[lo], b = smem[hi];
+          if ((a > b) == up) {
+            smem[lo] = b;
+            smem[hi] = a;
+          }
         }
+        const uint32_t next = stride > 1 ? stride >> 1 : size;  // the next stage's stride
+        if (stride <= 32 && next <= 32)
+          __syncwarp();
+        else
+          __syncthreads();
       }
-      __syncthreads();
     }
+    __syncthreads();
   }
   // 3. Counts of the base data sets: N - (first index with value >= |ybar_0|).
   uint32_t my_counts[kWiMaxPerThread];
@@ -94,7 +197,7 @@ __global__ void __launch_bounds__(kWiThreads) weakinf_kernel(
       uint32_t lo = 0, hi = N;  // search in [0, N)
       while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (smem[mid] < b)
+        if (smem[blocked ? wi_phys(mid) : mid] < b)
           lo = mid + 1;
         else
           hi = mid;
