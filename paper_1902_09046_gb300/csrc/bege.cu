@@ -192,8 +192,9 @@ constexpr float kCfTiny = 1e-30f;           // modified Lentz's floor for d and 
 //   Q <= exp(-x + a ln x - lgamma(a)) / (x + 1 - max(a, 1))     (x > a - 1)
 // is below 2^-56, 1 - Q rounds to 1 whatever Q is, and 1 is returned.  The
 // branches are decided on binary32 copies of x and a.  Each loop is bounded
-// by kGammaMaxIter terms.
-__device__ DF gammainc_p_df(float af, DF a_df, DF lga, DF x, const DF* __restrict__ inv, const DfTables& dtab) {
+// by kGammaMaxIter terms.  Not inlined: its three call sites share one copy,
+// which keeps the density kernel's code within the instruction cache.
+__device__ __noinline__ DF gammainc_p_df(float af, DF a_df, DF lga, DF x, const DF* __restrict__ inv, const DfTables& dtab) {
   if (!(x.hi > 0.0f)) return DF{0.0f, 0.0f};
   const DF lead = df_add(df_mul(a_df, df_log(x, dtab)), df_neg(df_add(x, lga)));  // a ln x - x - lgamma(a)
   const float xf = x.hi;
@@ -295,6 +296,18 @@ __global__ void __launch_bounds__(256) bege_tasks(const double* __restrict__ the
   }
 }
 
+// Negative-shock node j (1..100) of task K: its coordinate x0 and whether its
+// difference comes from the Taylor form, from both values, or is zero (both
+// values below 1e-297: P(n, x) <= e^(n ln x - x - lgamma(n)) (n + 1) / n for
+// x < n).
+__device__ __forceinline__ int node_kind(const BegeTask& K, int j, float delta_f, float nf, float lgn_f, DF& x0) {
+  x0 = df_add(K.ya, df_mul_f(K.yb, static_cast<float>(j - 1)));
+  const float xm = x0.hi + delta_f;
+  if (delta_f <= kTaylorMaxDelta && x0.hi >= kTaylorEdge * delta_f * fmaxf(1.0f, fabsf(K.nm1.hi))) return kTaylor;
+  if (!(xm > 0.0f) || (xm < nf && nf * __logf(xm) - xm - lgn_f < -700.0f)) return kNone;
+  return kTwoValues;
+}
+
 // f(u_t) for task (i, t) per warp.  Lane l owns grid nodes j = l + 32 k,
 // k = 0..3 (j <= 100): it evaluates P(p, .) at x_j and, for j >= 1, the
 // central difference over u +- h of the node's factor [1 - P(n, .)]; the
@@ -330,28 +343,15 @@ bege_density(uint32_t np, uint32_t T, double inv_2h, const DfTables* __restrict_
     const BegeTask K = tasks[task];
     const float delta_f = 0.5f * K.two_delta.hi;
     const float pf = K.p.hi;
-    // Each node's decision between the Taylor form and the two values, made
-    // once: the n table is needed only where some node of the warp is not a
-    // Taylor node.
-    DF x0s[4];
-    int kind[4];  // kTaylor, kTwoValues or kNone (both values below 1e-297)
+    // The n table is needed only where some node of the warp takes both
+    // values.
     bool near_edge = false;
     const float nf = K.nm1.hi + 1.0f, lgn_f = K.lgn.hi;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int j = static_cast<int>(lane) + 32 * k;
-      x0s[k] = df_add(K.ya, df_mul_f(K.yb, static_cast<float>(j - 1)));
-      const float xm = x0s[k].hi + delta_f;
-      if (delta_f <= kTaylorMaxDelta && x0s[k].hi >= kTaylorEdge * delta_f * fmaxf(1.0f, fabsf(K.nm1.hi))) {
-        kind[k] = kTaylor;
-      } else if (!(xm > 0.0f) || (xm < nf && nf * __logf(xm) - xm - lgn_f < -700.0f)) {
-        // P(n, x) <= e^(n ln x - x - lgamma(n)) (n + 1) / n for x < n: both
-        // values are below 1e-297 (and no table is needed).
-        kind[k] = kNone;
-      } else {
-        kind[k] = kTwoValues;
-        if (j >= 1 && j <= kBegeNw) near_edge = true;
-      }
+      DF x0;
+      if (j >= 1 && j <= kBegeNw && node_kind(K, j, delta_f, nf, lgn_f, x0) == kTwoValues) near_edge = true;
     }
     const bool fill_n = __any_sync(0xFFFFFFFFu, near_edge);
     const DF n_df = df_add_f(K.nm1, 1.0f);
@@ -363,8 +363,8 @@ bege_density(uint32_t np, uint32_t T, double inv_2h, const DfTables* __restrict_
     __syncwarp();
     DF acc = DF{0.0f, 0.0f};     // F(u + h) - F(u - h): a sum of non-negative terms
     DF F_last = DF{0.0f, 0.0f};  // F at node 32 k + 31 of the previous group (lane 31's value)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {  // one copy of the node code: it is large
       const int j = static_cast<int>(lane) + 32 * k;
       const bool live = j <= kBegeNw;
       DF F = DF{0.0f, 0.0f};
@@ -374,9 +374,10 @@ bege_density(uint32_t np, uint32_t T, double inv_2h, const DfTables* __restrict_
       F_last = DF{__shfl_sync(0xFFFFFFFFu, F.hi, 31), __shfl_sync(0xFFFFFFFFu, F.lo, 31)};
       if (live && j >= 1) {
         // [1 - P(n, x0 - delta)] - [1 - P(n, x0 + delta)], x0 = (w_{j-1} - u + n sn) / sn.
-        const DF x0 = x0s[k];
+        DF x0;
+        const int kind = node_kind(K, j, delta_f, nf, lgn_f, x0);
         DF dG;
-        if (kind[k] == kTaylor) {
+        if (kind == kTaylor) {
           // Gamma density g = x^(n-1) e^-x / Gamma(n).  With the derivatives of
           // ln g, L1 = (n-1)/x - 1, L2 = -(n-1)/x^2, L3 = 2(n-1)/x^3 and
           // L4 = -6(n-1)/x^4: g2/g = L1^2 + L2 and
@@ -397,7 +398,7 @@ bege_density(uint32_t np, uint32_t T, double inv_2h, const DfTables* __restrict_
                              (L1 * L1 * (L1 * L1 + 6.0f * L2) + 4.0f * L1 * L3 + 3.0f * L2 * L2 + L4);
             dG = df_scale(df_mul(g, df_add_f(K.two_delta, K.two_delta.hi * (c2 + c4))), m);
           }
-        } else if (kind[k] == kNone) {
+        } else if (kind == kNone) {
           dG = DF{0.0f, 0.0f};
         } else {
           // Both values in double-float.  Their relative difference is at
