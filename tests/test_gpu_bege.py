@@ -58,12 +58,12 @@ def _shape_sums(theta, r):
     return out
 
 
-def _compare(theta, r, ll_gpu, logf_gpu):
-    ll_o, dens = oracle.bege_loglik(theta, r, H, want_dens=True)
+def _compare(theta, r, ll_gpu, logf_gpu, h=H):
+    ll_o, dens = oracle.bege_loglik(theta, r, h, want_dens=True)
     fin_o, fin_g = np.isfinite(ll_o), np.isfinite(ll_gpu)
     s_t = _shape_sums(theta, r)
     with np.errstate(divide="ignore", invalid="ignore"):
-        noise = 1e-13 * (1 + s_t * np.log(2 + s_t)) / H      # absolute rounding scale of f_t
+        noise = 1e-13 * (1 + s_t * np.log(2 + s_t)) / h      # absolute rounding scale of f_t
         tol_t = np.where(dens > 0, noise / dens, 0.0)
     # A particle may end (-inf) on one side only where the deciding step's
     # density is within the rounding scale on the other side.
@@ -144,3 +144,30 @@ def test_invalid_arguments():
     assert lib.bege_loglik(P(th), 4, P(r), 8, H, P(ll), None, P(ws), ws_bytes - 1, None) != 0
     assert lib.bege_loglik(None, 4, P(r), 8, H, P(ll), None, P(ws), ws_bytes, None) != 0
     assert lib.bege_loglik(P(th), 4, P(r), 8, H, P(ll), None, P(ws), ws_bytes, None) == 0
+
+
+def test_extreme_regimes():
+    """Columns that drive every branch of the per-node code: shapes in the
+    hundreds (series past the reciprocal table, continued fraction past
+    a + 66); a negative shape below 1 (singular density at the support edge);
+    small sigma_n, whose delta = h / sigma_n is inside the Taylor bound at
+    h = 1e-5 and above it at h = 1e-3 (every node takes both values)."""
+    binding = require_gpu()
+    ref = np.array(W.BEGE_THETA_REF)
+    cols = []
+    c = ref.copy(); c[0], c[2] = 8.0, 0.99; cols.append(c)                          # p up to ~400
+    c = ref.copy(); c[5], c[7] = 5.0, 0.99; cols.append(c)                          # n up to ~250
+    c = ref.copy(); c[0], c[2], c[5], c[7] = 8.0, 0.99, 5.0, 0.99; cols.append(c)   # both
+    c = ref.copy(); c[5], c[7], c[8], c[9] = 0.05, 0.1, 1e-4, 1e-4; cols.append(c)   # n ~ 0.06
+    # small sigma_n (delta 0.005 / 0.5 and 0.002 / 0.2) with a positive shock wide enough to cover the
+    # returns (its support starts at -p sigma_p; the negative shock adds almost no left tail here)
+    c = ref.copy(); c[0], c[1], c[6], c[8], c[9] = 2.0, 0.05, 2e-3, 1e-6, 1e-6; cols.append(c)
+    c = ref.copy(); c[0], c[1], c[6], c[8], c[9] = 3.0, 0.06, 5e-3, 1e-6, 1e-6; cols.append(c)
+    theta = np.stack(cols, axis=1)
+    r = W.bege_returns(T=60, seed=13)
+    for h in (H, 1e-3):
+        out = binding.bege_loglik(torch.from_numpy(theta).cuda(), torch.from_numpy(r).cuda(), h, want_logf=True)
+        n_fin, n_edge, err, worst = _compare(theta, r, to_np(out["ll"]), to_np(out["logf"]), h=h)
+        assert n_fin == theta.shape[1], (h, n_fin)
+        print(f"BEGE extreme regimes, h = {h:g}: {n_fin} finite of {theta.shape[1]}, {n_edge} edge, "
+              f"max |dll| {err:.3g}, worst err/tol {worst:.3f}")
