@@ -10,10 +10,13 @@
 // mean and variance with Chan's pairwise update in a fixed order.
 //
 // Threshold mode (k = 0) skips the radix passes: the key of epsilon itself is
-// the cut.  Ties at the cut go to the smaller index in both modes.
+// the cut.  Ties at the cut go to the smaller index in both modes.  Up to
+// 24576 distances one CTA runs the same radix select and a round-by-round
+// compaction: a single launch for the many small jobs of a serving mix.
 #include <math.h>
 #include <string.h>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace ppabc {
@@ -69,10 +72,11 @@ struct WsLayout {
 };
 
 // Order-preserving image of a binary64 value: -0 maps to +0 and every NaN to
-// the largest key.
+// the largest key.  Integer operations only (a binary64 NaN test would go to
+// this GPU's narrow FP64 pipe, which a one-CTA selection feels).
 __device__ __forceinline__ unsigned long long dist_key(double d) {
-  if (isnan(d)) return 0xFFFFFFFFFFFFFFFFull;
   unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+  if ((b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull) return 0xFFFFFFFFFFFFFFFFull;  // NaN
   if (b == 0x8000000000000000ull) b = 0ull;
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
@@ -458,135 +462,235 @@ __global__ void __launch_bounds__(kTileThreads) select_moments(const MomentPart*
   }
 }
 
-// ---------------------------------------------------------------------------
-// Small inputs (n <= kSmallMax): the whole selection in one CTA.  Keys and
-// indices are bitonic-sorted in shared memory (ties by index), the accepted
-// samples are flagged by index, then compacted in index order; the moments
-// are a fixed-order block reduction.  One launch instead of eleven matters
-// for the many small jobs of a serving mix.
-// ---------------------------------------------------------------------------
-constexpr int kSmallThreads = 1024;
-constexpr int kSmallMax = 4096;
-constexpr int kSmallPer = kSmallMax / kSmallThreads;
-
-template <typename T>
-__device__ __forceinline__ T block_sum_fixed(T v, T* red /* >= 32 */) {
+// Posterior mean and variance from the per-thread double-float sums of
+// (theta - c) and (theta - c)^2 about a shift c (the first accepted theta):
+// a fixed-order warp shuffle tree, then the warps in order in thread 0;
+// mean = c + S1 / k and M2 = S2 - S1^2 / k in binary64.  Everything before
+// the last step runs on the binary32 pipes (a one-CTA binary64 reduction
+// would queue on this GPU's narrow FP64 pipe).  s_S1, s_S2 hold one value
+// per warp and dimension; the result is written by thread 0.
+template <int kWarps>
+__device__ __forceinline__ void finish_moments(DF (&S1)[3], DF (&S2)[3], const float (&c)[3],
+                                               unsigned long long k, DF (*s_S1)[kWarps], DF (*s_S2)[kWarps],
+                                               double* post_out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      S1[d] = df_add(S1[d], DF{__shfl_xor_sync(0xFFFFFFFFu, S1[d].hi, o), __shfl_xor_sync(0xFFFFFFFFu, S1[d].lo, o)});
+      S2[d] = df_add(S2[d], DF{__shfl_xor_sync(0xFFFFFFFFu, S2[d].hi, o), __shfl_xor_sync(0xFFFFFFFFu, S2[d].lo, o)});
+    }
+    if (lane == 0) {
+      s_S1[d][warp] = S1[d];
+      s_S2[d][warp] = S2[d];
+    }
+  }
   __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  T t = 0;
-  for (int w = 0; w < kSmallThreads / 32; ++w) t += red[w];
-  return t;
+  if (threadIdx.x == 0 && post_out) {
+    const double kk = static_cast<double>(k);
+    for (int d = 0; d < 3; ++d) {
+      DF a = DF{0.0f, 0.0f}, b = DF{0.0f, 0.0f};
+      for (int w = 0; w < kWarps; ++w) {
+        a = df_add(a, s_S1[d][w]);
+        b = df_add(b, s_S2[d][w]);
+      }
+      const double s1 = df_to_double(a), s2 = df_to_double(b);
+      post_out[d] = k > 0 ? static_cast<double>(c[d]) + s1 / kk : nan("");
+      post_out[3 + d] = k > 1 ? (s2 - s1 * s1 / kk) / (kk - 1.0) : nan("");
+    }
+  }
 }
 
+// Adds (theta - c) and (theta - c)^2 to the double-float sums; each
+// difference is exact as a two-sum.
+__device__ __forceinline__ void add_moment(DF (&S1)[3], DF (&S2)[3], const float (&th)[3], const float (&c)[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const DF r = df_two_sum(th[d], -c[d]);
+    S1[d] = df_add(S1[d], r);
+    S2[d] = df_add(S2[d], df_sqr(r));
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Up to kMidMax distances: the whole selection in one CTA, reading the
+// distances from global memory (L2) on every pass.  The
+// radix select of the large path (six 11-bit passes with warp-aggregated
+// shared histograms) runs in the CTA; the compaction walks the indices in
+// rounds of 16 per thread, carrying the equal-key rank and the output
+// position from round to round; the moments are double-float sums about the
+// first accepted theta (binary32 pipes: a one-CTA binary64 reduction would
+// queue on this GPU's narrow FP64 pipe).  One launch instead of eleven.
+// ---------------------------------------------------------------------------
+constexpr int kMidThreads = 1024;
+constexpr uint32_t kMidMax = 24576;  // above this the multi-CTA passes are faster
+constexpr int kMidPer = 16;
+constexpr uint32_t kMidRound = kMidThreads * kMidPer;
+
 template <bool kTheta>
-__global__ void __launch_bounds__(kSmallThreads) select_small(
-    const double* __restrict__ dist, uint32_t n, uint32_t P, unsigned long long k, bool threshold,
+__global__ void __launch_bounds__(kMidThreads) select_mid(
+    const double* __restrict__ dist, uint32_t n, unsigned long long k, bool threshold,
     unsigned long long cut_thr, double eps_thr, const __grid_constant__ OUConst prm, uint32_t base,
     const float* __restrict__ theta, uint32_t* __restrict__ idx_out, float4* __restrict__ rec_out,
     unsigned long long cap, unsigned long long* __restrict__ n_acc_out, double* __restrict__ eps_out,
     double* __restrict__ post_out) {
-  extern __shared__ unsigned long long sm_keys[];  // P keys, then P indices, then n flags
-  uint32_t* sm_idx = reinterpret_cast<uint32_t*>(sm_keys + P);
-  unsigned char* sm_flag = reinterpret_cast<unsigned char*>(sm_idx + P);
-  __shared__ unsigned int scan_smem[kSmallThreads / 32];
-  __shared__ double red[kSmallThreads / 32];
-  for (uint32_t i = threadIdx.x; i < P; i += kSmallThreads) {
-    sm_keys[i] = i < n ? dist_key(dist[i]) : 0xFFFFFFFFFFFFFFFFull;
-    sm_idx[i] = i < n ? i : 0xFFFFFFFFu;
-    if (i < n) sm_flag[i] = 0;
-  }
-  __syncthreads();
+  __shared__ unsigned int h[kBins];
+  __shared__ unsigned int scan_smem[kMidThreads / 32];
+  __shared__ unsigned long long scan64[kMidThreads / 32];
+  __shared__ unsigned long long s_prefix, s_mask, s_krem;
+  __shared__ unsigned int acc_bits[kMidMax / 32];
+  __shared__ float s_shift[3];
+  __shared__ DF s_S1[3][kMidThreads / 32], s_S2[3][kMidThreads / 32];
+  const int lane = threadIdx.x & 31;
+  unsigned long long prefix = 0ull, mask = 0ull, krem = k;
+  // 1. Radix select of the k-th smallest key (skipped in threshold mode).
   if (!threshold) {
-    for (uint32_t size = 2; size <= P; size <<= 1) {
-      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-        for (uint32_t t = threadIdx.x; t < (P >> 1); t += kSmallThreads) {
-          const uint32_t lo = 2 * t - (t & (stride - 1));
-          const uint32_t hi = lo + stride;
-          const bool up = (lo & size) == 0;
-          const unsigned long long ka = sm_keys[lo], kb = sm_keys[hi];
-          const uint32_t ia = sm_idx[lo], ib = sm_idx[hi];
-          const bool greater = ka > kb || (ka == kb && ia > ib);
-          if (greater == up) {
-            sm_keys[lo] = kb;
-            sm_keys[hi] = ka;
-            sm_idx[lo] = ib;
-            sm_idx[hi] = ia;
-          }
+    for (int pass = 0; pass < kNumPasses; ++pass) {
+      const int shift = kPassShift[pass];
+      const unsigned long long dmask = (1ull << kPassBits[pass]) - 1ull;
+      for (int b = threadIdx.x; b < kBins; b += kMidThreads) h[b] = 0u;
+      __syncthreads();
+      for (uint32_t b0 = 0; b0 < n; b0 += kMidThreads) {  // uniform bound: every lane reaches the match
+        const uint32_t i = b0 + threadIdx.x;
+        unsigned int bin = 0xFFFFFFFFu;
+        if (i < n) {
+          const unsigned long long key = dist_key(__ldg(dist + i));
+          if ((key & mask) == prefix) bin = static_cast<unsigned int>((key >> shift) & dmask);
         }
-        __syncthreads();
+        const unsigned int peers = __match_any_sync(0xFFFFFFFFu, bin);
+        if (bin != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&h[bin], __popc(peers));
+      }
+      __syncthreads();
+      constexpr int kPer = kBins / kMidThreads;  // bins owned by one thread
+      unsigned int c[kPer];
+      unsigned int mine = 0;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        c[q] = h[threadIdx.x * kPer + q];
+        mine += c[q];
+      }
+      unsigned int total;
+      const unsigned int before = block_exclusive_scan<unsigned int>(mine, &total, scan_smem);
+      if (before < krem && krem <= static_cast<unsigned long long>(before) + mine) {
+        unsigned long long run = before;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+          if (run < krem && krem <= run + c[q]) {
+            s_prefix = prefix | (static_cast<unsigned long long>(threadIdx.x * kPer + q) << shift);
+            s_mask = mask | (dmask << shift);
+            s_krem = krem - run;
+          }
+          run += c[q];
+        }
+      }
+      __syncthreads();
+      prefix = s_prefix;
+      mask = s_mask;
+      krem = s_krem;
+    }
+  }
+  const unsigned long long cut = threshold ? cut_thr : prefix;
+  if (threshold) krem = 0xFFFFFFFFFFFFFFFFull;
+  // 2. Compaction in index order, 16 consecutive indices per thread and round;
+  // the accepted indices are also marked in a bit set for the moments.
+  for (uint32_t w = threadIdx.x; w < kMidMax / 32; w += kMidThreads) acc_bits[w] = 0u;
+  if (threadIdx.x < 3) s_shift[threadIdx.x] = 0.0f;
+  __syncthreads();
+  unsigned long long carry_eq = 0ull, carry_acc = 0ull;
+  for (uint32_t rb = 0; rb < n; rb += kMidRound) {
+    const uint32_t t0 = rb + threadIdx.x * kMidPer;
+    unsigned int flags = 0, eqmask = 0, my_eq = 0;
+#pragma unroll
+    for (int q = 0; q < kMidPer; ++q) {
+      const uint32_t i = t0 + q;
+      if (i < n) {
+        const unsigned long long key = dist_key(dist[i]);
+        if (key < cut) flags |= 1u << q;
+        if (key == cut) {
+          eqmask |= 1u << q;
+          ++my_eq;
+        }
       }
     }
-    for (uint32_t t = threadIdx.x; t < k; t += kSmallThreads) sm_flag[sm_idx[t]] = 1;
-  } else {
-    for (uint32_t i = threadIdx.x; i < n; i += kSmallThreads) sm_flag[i] = sm_keys[i] <= cut_thr;
+    unsigned long long tot_eq;
+    const unsigned long long eq_rank0 =
+        carry_eq + block_exclusive_scan<unsigned long long>(my_eq, &tot_eq, scan64);
+    {
+      unsigned long long r = eq_rank0;
+#pragma unroll
+      for (int q = 0; q < kMidPer; ++q) {
+        if (eqmask & (1u << q)) {
+          if (r < krem) flags |= 1u << q;
+          ++r;
+        }
+      }
+    }
+    unsigned long long tot_acc;
+    unsigned long long pos =
+        carry_acc + block_exclusive_scan<unsigned long long>(__popc(flags), &tot_acc, scan64);
+    // 16 indices starting at a multiple of 16: half of one bit-set word
+    if (flags) atomicOr(&acc_bits[t0 >> 5], flags << (t0 & 16u));
+#pragma unroll
+    for (int q = 0; q < kMidPer; ++q) {
+      if (flags & (1u << q)) {
+        const uint32_t i = t0 + q;
+        float th[3];
+        if (kTheta) {
+          th[0] = theta[i];
+          th[1] = theta[static_cast<size_t>(n) + i];
+          th[2] = theta[2 * static_cast<size_t>(n) + i];
+        } else {
+          ou_prior(prm, base + i, th[0], th[1], th[2]);
+        }
+        if (pos == 0) {
+          s_shift[0] = th[0];
+          s_shift[1] = th[1];
+          s_shift[2] = th[2];
+        }
+        if (pos < cap) {
+          idx_out[pos] = i;
+          rec_out[pos] = make_float4(th[0], th[1], th[2], static_cast<float>(dist[i]));
+        }
+        ++pos;
+      }
+    }
+    carry_eq += tot_eq;
+    carry_acc += tot_acc;
   }
   __syncthreads();
-  // Compaction in index order: thread t owns indices 4t .. 4t+3.
-  unsigned int flags = 0;
-#pragma unroll
-  for (int q = 0; q < kSmallPer; ++q) {
-    const uint32_t i = threadIdx.x * kSmallPer + q;
-    if (i < n && sm_flag[i]) flags |= 1u << q;
-  }
-  unsigned int total;
-  const unsigned int pos0 = block_exclusive_scan<unsigned int>(__popc(flags), &total, scan_smem);
-  float th[kSmallPer][3];
-  double sum[3] = {0.0, 0.0, 0.0};
-  unsigned long long pos = pos0;
-#pragma unroll
-  for (int q = 0; q < kSmallPer; ++q) {
-    if (flags & (1u << q)) {
-      const uint32_t i = threadIdx.x * kSmallPer + q;
-      float a, b, c;
-      if (kTheta) {
-        a = theta[i];
-        b = theta[static_cast<size_t>(n) + i];
-        c = theta[2 * static_cast<size_t>(n) + i];
-      } else {
-        ou_prior(prm, base + i, a, b, c);
-      }
-      th[q][0] = a;
-      th[q][1] = b;
-      th[q][2] = c;
-      sum[0] += a;
-      sum[1] += b;
-      sum[2] += c;
-      if (pos < cap) {
-        idx_out[pos] = i;
-        rec_out[pos] = make_float4(a, b, c, static_cast<float>(dist[i]));
-      }
-      ++pos;
-    }
-  }
-  double mean[3], var[3];
-  for (int d = 0; d < 3; ++d) {
-    const double tsum = block_sum_fixed<double>(sum[d], red);
-    mean[d] = total ? tsum / static_cast<double>(total) : 0.0;
-  }
-  for (int d = 0; d < 3; ++d) {
-    double m2 = 0.0;
-#pragma unroll
-    for (int q = 0; q < kSmallPer; ++q) {
+  // 3. Moments about the first accepted theta c: the sums of (theta - c) and
+  // (theta - c)^2 in double-float (each difference exact as a two-sum), per
+  // thread in index order, then a fixed-order tree over the CTA;
+  // mean = c + S1 / k and M2 = S2 - S1^2 / k in binary64.  The accepted theta
+  // are formed again from their counters (or read again).
+  const float cs[3] = {s_shift[0], s_shift[1], s_shift[2]};
+  DF S1[3] = {DF{0.0f, 0.0f}, DF{0.0f, 0.0f}, DF{0.0f, 0.0f}};
+  DF S2[3] = {DF{0.0f, 0.0f}, DF{0.0f, 0.0f}, DF{0.0f, 0.0f}};
+  for (uint32_t rb = 0; rb < n; rb += kMidRound) {
+    const uint32_t t0 = rb + threadIdx.x * kMidPer;
+    const unsigned int flags = t0 < n ? (acc_bits[t0 >> 5] >> (t0 & 16u)) & 0xFFFFu : 0u;
+#pragma unroll 1
+    for (int q = 0; q < kMidPer; ++q) {
       if (flags & (1u << q)) {
-        const double r = static_cast<double>(th[q][d]) - mean[d];
-        m2 = fma(r, r, m2);
+        const uint32_t i = t0 + q;
+        float th[3];
+        if (kTheta) {
+          th[0] = theta[i];
+          th[1] = theta[static_cast<size_t>(n) + i];
+          th[2] = theta[2 * static_cast<size_t>(n) + i];
+        } else {
+          ou_prior(prm, base + i, th[0], th[1], th[2]);
+        }
+        add_moment(S1, S2, th, cs);
       }
     }
-    var[d] = block_sum_fixed<double>(m2, red);
   }
+  finish_moments<kMidThreads / 32>(S1, S2, cs, carry_acc, s_S1, s_S2, post_out);
   if (threadIdx.x == 0) {
-    *n_acc_out = total;
-    if (eps_out) *eps_out = threshold ? eps_thr : key_to_double(sm_keys[k - 1]);
-    if (post_out) {
-      for (int d = 0; d < 3; ++d) {
-        post_out[d] = total > 0 ? mean[d] : nan("");
-        post_out[3 + d] = total > 1 ? var[d] / static_cast<double>(total - 1) : nan("");
-      }
-    }
+    *n_acc_out = carry_acc;
+    if (eps_out) *eps_out = threshold ? eps_thr : key_to_double(cut);
   }
 }
 
@@ -607,29 +711,18 @@ cudaError_t launch_select(const double* dist, uint32_t n, uint64_t k, double eps
                           float* rec_out, uint64_t cap, uint64_t* n_acc_out, double* eps_out,
                           double* post_out, void* ws, cudaStream_t s) {
   const bool threshold = (k == 0);
-  if (n > 0 && n <= static_cast<uint32_t>(kSmallMax)) {
-    uint32_t P = 2;
-    while (P < n) P <<= 1;
-    const size_t smem = P * (sizeof(unsigned long long) + sizeof(uint32_t)) + ((n + 15) & ~15u);
+  if (n > 0 && n <= kMidMax) {
     const unsigned long long cut = threshold ? host_dist_key(eps) : 0ull;
-    cudaError_t e;
-    if (theta) {
-      e = cudaFuncSetAttribute(select_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(smem));
-      if (e != cudaSuccess) return e;
-      select_small<true><<<1, kSmallThreads, smem, s>>>(
-          dist, n, P, k, threshold, cut, eps, P_, static_cast<uint32_t>(base), theta, idx_out,
-          reinterpret_cast<float4*>(rec_out), cap, reinterpret_cast<unsigned long long*>(n_acc_out),
-          eps_out, post_out);
-    } else {
-      e = cudaFuncSetAttribute(select_small<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(smem));
-      if (e != cudaSuccess) return e;
-      select_small<false><<<1, kSmallThreads, smem, s>>>(
-          dist, n, P, k, threshold, cut, eps, P_, static_cast<uint32_t>(base), theta, idx_out,
-          reinterpret_cast<float4*>(rec_out), cap, reinterpret_cast<unsigned long long*>(n_acc_out),
-          eps_out, post_out);
-    }
+    if (theta)
+      select_mid<true><<<1, kMidThreads, 0, s>>>(dist, n, k, threshold, cut, eps, P_, static_cast<uint32_t>(base),
+                                                 theta, idx_out, reinterpret_cast<float4*>(rec_out), cap,
+                                                 reinterpret_cast<unsigned long long*>(n_acc_out), eps_out,
+                                                 post_out);
+    else
+      select_mid<false><<<1, kMidThreads, 0, s>>>(dist, n, k, threshold, cut, eps, P_, static_cast<uint32_t>(base),
+                                                  theta, idx_out, reinterpret_cast<float4*>(rec_out), cap,
+                                                  reinterpret_cast<unsigned long long*>(n_acc_out), eps_out,
+                                                  post_out);
     return cudaGetLastError();
   }
   const WsLayout L(n);

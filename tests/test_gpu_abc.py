@@ -134,9 +134,12 @@ def _select_cases():
     yield "one", np.array([0.5])
     yield "specials", np.array([np.nan, 0.0, -0.0, np.inf, 1.0, 0.0, np.nan, 2.0, np.inf, 1e-300])
     yield "large", rng.exponential(size=1 << 21)
-    # around the single-CTA / multi-kernel boundary (4096 distances)
+    # small sizes with ties (one CTA)
     for n in (4095, 4096, 4097, 2049):
         yield f"edge{n}", np.round(rng.exponential(size=n), 2)
+    # around the one-CTA selection's limit (24576 distances), heavy ties
+    for n in (24575, 24576, 24577, 30001):
+        yield f"mid{n}", np.round(rng.exponential(size=n), 1)
 
 
 @pytest.mark.parametrize("case", [c for c, _ in _select_cases()])
