@@ -50,9 +50,108 @@ __global__ void __launch_bounds__(kEmThreads, 10) em_ou_fused_x2(const __grid_co
   if (i1 < n) dist_out[i1] = d[1];
 }
 
+// Small launches (n up to kPipeMaxN samples): a warp-specialised pipeline.
+// With few samples the two-path kernel leaves most of the GPU idle and each
+// warp waits on its own dependency chain.  Here a CTA owns 32 samples: warps
+// 1..kPipeProducers draw the scaled normals of every counter block for those
+// samples (lane = sample) into a double-buffered ring in shared memory, kPipeRound
+// blocks per round, while warp 0 runs the samples' Euler-Maruyama paths
+// (lane = sample) over the previous round's blocks.  The path arithmetic is
+// ou_path's, block by block in the same order, so the distances are bit for
+// bit those of the other kernels.  Rounds end at a CTA barrier; nothing spins.
+constexpr int kPipeProducers = 6;
+constexpr int kPipeRound = 12;
+constexpr int kPipeThreads = 32 * (1 + kPipeProducers);
+
+__global__ void __launch_bounds__(kPipeThreads) em_ou_pipe(const __grid_constant__ OUConst P, uint32_t base,
+                                                           uint32_t n, double* __restrict__ dist_out) {
+  __shared__ float4 ring[2][kPipeRound][32];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t i = blockIdx.x * 32 + lane;
+  const bool valid = i < n;
+  const uint32_t g = base + (valid ? i : n - 1);
+  float th1, th2, th3;
+  ou_prior(P, g, th1, th2, th3);
+  const float c = th3 * P.sqrt_dt;
+  const uint32_t S = P.n_steps, n_obs = P.n_obs;
+  const uint32_t n_blocks = (P.s_obs[n_obs - 1] + 3u) >> 2;  // blocks up to the last observation
+  const uint32_t rounds = (n_blocks + kPipeRound - 1) / kPipeRound;
+  if (warp > 0) {
+    const PhiloxStream stream = philox_stream(P.keys, g, P.sub, kTagPath);
+    for (uint32_t r = 0; r <= rounds; ++r) {
+      if (r < rounds) {
+        for (uint32_t q = warp - 1; q < static_cast<uint32_t>(kPipeRound); q += kPipeProducers) {
+          const uint32_t b = r * kPipeRound + q;
+          if (b < n_blocks) ring[r & 1u][q][lane] = scaled_normals_of(philox_block(stream, P.keys, b), c);
+        }
+      }
+      __syncthreads();
+    }
+    return;
+  }
+  // Warp 0: ou_path's walk, one counter block at a time.
+  const float k = th1 * P.dt;
+  float Y = P.x0 - th2;
+  float comp;
+  {
+    const float bb = Y - P.x0;
+    const float err = (P.x0 - (Y - bb)) + (-th2 - bb);
+    comp = -err;
+  }
+  const double th2d = static_cast<double>(th2);
+  double acc = 0.0;
+  const Em4 E4 = em4_constants(k);
+  uint32_t s = 0, b = 0, j = 0, s_next = 0, b_end = 0;
+  bool seg = true;  // a new run of whole blocks starts at block b
+  for (uint32_t r = 0; r <= rounds; ++r) {
+    if (r > 0) {
+      for (uint32_t q = 0; q < static_cast<uint32_t>(kPipeRound) && j < n_obs; ++q) {
+        if ((r - 1) * kPipeRound + q >= n_blocks) break;
+        const float4 z = ring[(r - 1) & 1u][q][lane];
+        if (seg) {
+          s_next = P.s_obs[j];
+          b_end = b + (s_next > s + 4u ? (s_next - s - 1u) >> 2 : 0u);
+          s += (b_end - b) << 2;
+          seg = false;
+        }
+        if (b < b_end) {
+          em_block4(Y, comp, E4, z);
+          ++b;
+          continue;
+        }
+        ++b;  // the block holding step s_next (and possibly later observation steps)
+        const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          if (s < S) {
+            em_step(Y, comp, k, zz[l]);
+            ++s;
+            if (s == s_next) {
+              const double x = th2d + (static_cast<double>(Y) - static_cast<double>(comp));
+              const double rr = x - P.y[j];
+              acc = fma(rr, rr, acc);
+              ++j;
+              s_next = (j < n_obs) ? P.s_obs[j] : 0xFFFFFFFFu;
+            }
+          }
+        }
+        seg = true;
+      }
+    }
+    __syncthreads();
+  }
+  if (valid) dist_out[i] = sqrt(acc);
+}
+
+constexpr uint32_t kPipeMaxN = 49152;  // above about this the two-path kernel is faster
+
 cudaError_t launch_em_ou(const OUConst& P, uint64_t base, uint32_t n, float* theta_out,
                          double* summ_out, double* dist_out, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
+  if (!theta_out && !summ_out && n <= kPipeMaxN) {
+    em_ou_pipe<<<(n + 31) / 32, kPipeThreads, 0, s>>>(P, static_cast<uint32_t>(base), n, dist_out);
+    return cudaGetLastError();
+  }
   if (!theta_out && !summ_out) {
     const dim3 grid2((n + 2 * kEmThreads - 1) / (2 * kEmThreads));
     em_ou_fused_x2<<<grid2, kEmThreads, 0, s>>>(P, static_cast<uint32_t>(base), n, dist_out);

@@ -107,6 +107,24 @@ def test_two_paths_per_thread_is_bit_identical(n):
     np.testing.assert_array_equal(to_np(a["dist"]), to_np(b["dist"]))
 
 
+@pytest.mark.parametrize("n_steps,n_obs,n", [(37, 10, 33), (1000, 1, 1), (4, 4, 129), (250, 32, 1000),
+                                             (101, 7, 4099), (7, 7, 65), (9, 3, 31), (1000, 10, 49152),
+                                             (1000, 10, 49153)])
+def test_small_launch_pipeline_is_bit_identical(n_steps, n_obs, n):
+    """Small launches without theta or summaries run the warp-specialised
+    pipeline (normals drawn by producer warps, paths walked by one warp);
+    every distance equals the one-path-per-thread kernel's, for step counts
+    that are not multiples of four and for several observations in one
+    counter block."""
+    binding = require_gpu()
+    model = workloads.ou_model(n_steps, t_end=0.01 * n_steps, n_obs=n_obs)
+    y = np.linspace(-0.5, 1.0, n_obs)
+    a = binding.abc_prior_predictive(model, y, n, 11, sample_base=5, want_theta=False)
+    b = binding.abc_prior_predictive(model, y, n, 11, sample_base=5, want_theta=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(to_np(a["dist"]), to_np(b["dist"]))
+
+
 def test_empty_and_invalid():
     binding = require_gpu()
     w = workloads.abc_small()
