@@ -11,8 +11,9 @@
 namespace ppabc {
 
 // Two data sets at once (lane q = data set q, streams S0 and S1 of the same
-// length): the normals come packed across the sets (normals_x2) and the sums
-// are Kahan-compensated on packed binary32 pairs:
+// length): the normals come packed across the sets (normals_x2); the four
+// normals of a counter block are summed pairwise and the block sums are
+// added with Kahan compensation on packed binary32 pairs:
 //   y = x - comp;  t = s + y;  comp = (t - s) - y;  s = t
 // (x - y formed as fma(y, -1, x), which rounds identically), then
 // ybar = lambda z_0 + (s - comp) / n in binary64.
@@ -34,14 +35,13 @@ __device__ __forceinline__ double2 dataset_ybar2(const PhiloxKeys& K, double lam
   float2 z[4];
   for (uint32_t b = 0; b < n_full; ++b) {
     normals_x2(philox_block(S0, K, b), philox_block(S1, K, b), z);
+    // a block's normals summed pairwise, then one compensated add
     if (b == 0) {
       z0 = z[0];
+      kahan_add2(s, comp, add2(add2(z[1], z[2]), z[3]));
     } else {
-      kahan_add2(s, comp, z[0]);
+      kahan_add2(s, comp, add2(add2(z[0], z[1]), add2(z[2], z[3])));
     }
-    kahan_add2(s, comp, z[1]);
-    kahan_add2(s, comp, z[2]);
-    kahan_add2(s, comp, z[3]);
   }
   if (rem) {
     normals_x2(philox_block(S0, K, n_full), philox_block(S1, K, n_full), z);
