@@ -283,6 +283,11 @@ int ppabc_batch_prepare(const ppabc_abc_job* h_jobs, uint32_t n_jobs,
     delete plan;
     return check_cuda(e, "occupancy query");
   }
+  e = select_prepare();  // before a graph capture of the launches
+  if (e != cudaSuccess) {
+    delete plan;
+    return check_cuda(e, "selection setup");
+  }
   plan->grid = std::max(1, sms) * std::max(1, per_sm);
   *plan_out = plan;
   return PPABC_OK;

@@ -32,6 +32,9 @@ cudaError_t launch_em_ou(const OUConst& P, uint64_t base, uint32_t n, float* the
 
 // Selection.
 size_t select_workspace_bytes(uint64_t n);
+// Raises the one-CTA selection's shared-memory limit on the current device
+// (once; launch_select calls it too).  Call before capturing launches.
+cudaError_t select_prepare();
 cudaError_t launch_select(const double* dist, uint32_t n, uint64_t k, double eps,
                           const OUConst& P, uint64_t base, const float* theta, uint32_t* idx_out,
                           float* rec_out, uint64_t cap, uint64_t* n_acc_out, double* eps_out,

@@ -4,17 +4,20 @@
 // distribution of the discrepancy (Sec. 3.1): accepting the k nearest means
 // epsilon is the k-th smallest distance.  This file finds it with an exact
 // MSD radix select over the order-preserving 64-bit image of each binary64
-// distance (6 histogram passes of 11/11/11/11/11/9 bits; the last CTA of a
-// pass picks the digit, so no host round trip), then writes the accepted
-// samples in index order with a two-level scan, and reduces the posterior
-// mean and variance with Chan's pairwise update in a fixed order.
+// distance (up to 6 histogram passes of 11/11/11/11/11/9 bits, ending once a
+// single key is left under the fixed bits; the last CTA of a pass picks the
+// digit, so no host round trip), then writes the accepted samples in index
+// order with a two-level scan, and reduces the posterior mean and variance
+// with Chan's pairwise update in a fixed order.
 //
 // Threshold mode (k = 0) skips the radix passes: the key of epsilon itself is
 // the cut.  Ties at the cut go to the smaller index in both modes.  Up to
-// 24576 distances one CTA runs the same radix select and a round-by-round
-// compaction: a single launch for the many small jobs of a serving mix.
+// 24576 distances one CTA does all of it from shared memory in a single
+// launch, for the many small jobs of a serving mix.
 #include <math.h>
 #include <string.h>
+
+#include <atomic>
 
 #include "dfloat.cuh"
 #include "internal.h"
@@ -29,6 +32,7 @@ constexpr int kTileThreads = 256;
 constexpr int kPerThread = 16;
 constexpr int kTile = kTileThreads * kPerThread;  // elements per compaction tile
 constexpr int kNumPasses = 6;
+constexpr int kHistChunk = 4;  // histogram loads in flight per thread
 __constant__ int kPassShift[kNumPasses] = {53, 42, 31, 20, 9, 0};
 __constant__ int kPassBits[kNumPasses] = {11, 11, 11, 11, 11, 9};
 
@@ -37,8 +41,9 @@ struct SelState {
   unsigned long long mask;    // which bits of prefix are fixed
   unsigned long long krem;    // rank still to reach among keys matching prefix
   unsigned int ticket;        // CTAs done in the current pass
-  unsigned int pad;
+  unsigned int done;          // one key matches prefix: the later passes return at once
   unsigned long long n_acc;
+  unsigned long long cut;     // full key of the k-th smallest, found by select_count once done
 };
 
 struct MomentPart {  // per-tile (count, mean, M2) of the accepted theta
@@ -74,11 +79,14 @@ struct WsLayout {
 // Order-preserving image of a binary64 value: -0 maps to +0 and every NaN to
 // the largest key.  Integer operations only (a binary64 NaN test would go to
 // this GPU's narrow FP64 pipe, which a one-CTA selection feels).
-__device__ __forceinline__ unsigned long long dist_key(double d) {
-  unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+__device__ __forceinline__ unsigned long long key_of_bits(unsigned long long b) {
   if ((b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull) return 0xFFFFFFFFFFFFFFFFull;  // NaN
   if (b == 0x8000000000000000ull) b = 0ull;
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ unsigned long long dist_key(double d) {
+  return key_of_bits(static_cast<unsigned long long>(__double_as_longlong(d)));
 }
 
 __device__ __forceinline__ double key_to_double(unsigned long long k) {
@@ -93,7 +101,9 @@ __global__ void select_init(SelState* st, unsigned int* hist, unsigned long long
     st->mask = 0ull;
     st->krem = k;
     st->ticket = 0u;
+    st->done = 0u;
     st->n_acc = 0ull;
+    st->cut = 0ull;
   }
 }
 
@@ -128,13 +138,16 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* smem /* >= w
 
 // One radix pass: histogram of the digit at `pass` over keys that match the
 // prefix fixed so far; the last CTA to finish picks the digit holding rank
-// krem and narrows the prefix.
+// krem and narrows the prefix.  Once that digit's bin holds a single key, the
+// k-th smallest is the one key matching the prefix, and the passes left
+// return without reading the distances.
 __global__ void __launch_bounds__(kHistThreads) select_hist(const double* __restrict__ dist,
                                                             uint32_t n, int pass, SelState* st,
                                                             unsigned int* hist) {
   __shared__ unsigned int h[kBins];
   __shared__ bool is_last;
   __shared__ unsigned int scan_smem[8];
+  if (st->done) return;
   const int shift = kPassShift[pass];
   const unsigned long long dmask = (1ull << kPassBits[pass]) - 1ull;
   for (int b = threadIdx.x; b < kBins; b += kHistThreads) h[b] = 0u;
@@ -144,17 +157,27 @@ __global__ void __launch_bounds__(kHistThreads) select_hist(const double* __rest
   // The loop bound is uniform across the CTA so every lane reaches the match.
   const int lane = threadIdx.x & 31;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kHistThreads;
-  for (uint64_t b0 = static_cast<uint64_t>(blockIdx.x) * kHistThreads; b0 < n; b0 += stride) {
-    const uint64_t i = b0 + threadIdx.x;
-    unsigned int bin = 0xFFFFFFFFu;
-    if (i < n) {
-      const unsigned long long key = dist_key(__ldg(dist + i));
-      if ((key & mask) == prefix) bin = static_cast<unsigned int>((key >> shift) & dmask);
+  for (uint64_t b0 = static_cast<uint64_t>(blockIdx.x) * kHistThreads; b0 < n; b0 += stride * kHistChunk) {
+    // kHistChunk keys loaded and binned per thread before their histogram
+    // adds, so that the loads are in flight together
+    unsigned int bin[kHistChunk];
+#pragma unroll
+    for (int j = 0; j < kHistChunk; ++j) {
+      const uint64_t i = b0 + j * stride + threadIdx.x;
+      const unsigned long long key = i < n ? dist_key(__ldg(dist + i)) : 0ull;
+      bin[j] = (i < n && (key & mask) == prefix) ? static_cast<unsigned int>((key >> shift) & dmask)
+                                                 : 0xFFFFFFFFu;
     }
-    // Distances crowd into few bins on the early passes: one shared atomic
-    // per distinct bin in the warp.
-    const unsigned int peers = __match_any_sync(0xFFFFFFFFu, bin);
-    if (bin != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&h[bin], __popc(peers));
+#pragma unroll
+    for (int j = 0; j < kHistChunk; ++j) {
+      // Distances crowd into few bins on the early passes: one shared atomic
+      // per distinct bin in the warp.  On the later passes few keys match the
+      // prefix, and warps without one skip the match.
+      if (__any_sync(0xFFFFFFFFu, bin[j] != 0xFFFFFFFFu)) {
+        const unsigned int peers = __match_any_sync(0xFFFFFFFFu, bin[j]);
+        if (bin[j] != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&h[bin[j]], __popc(peers));
+      }
+    }
   }
   __syncthreads();
   for (int b = threadIdx.x; b < kBins; b += kHistThreads)
@@ -187,6 +210,7 @@ __global__ void __launch_bounds__(kHistThreads) select_hist(const double* __rest
         st->prefix = prefix | (digit << shift);
         st->mask = mask | (dmask << shift);
         st->krem = krem - run;
+        if (c[q] == 1u) st->done = 1u;
       }
       run += c[q];
     }
@@ -196,13 +220,16 @@ __global__ void __launch_bounds__(kHistThreads) select_hist(const double* __rest
 
 // Per-tile counts of keys below and at the cut.
 __global__ void __launch_bounds__(kTileThreads) select_count(const double* __restrict__ dist,
-                                                             uint32_t n, const SelState* st,
+                                                             uint32_t n, SelState* st,
                                                              bool threshold,
                                                              unsigned long long cut_thr,
                                                              unsigned int* tile_less,
                                                              unsigned int* tile_eq) {
   __shared__ unsigned int s_less[kTileThreads / 32], s_eq[kTileThreads / 32];
+  // Keys compare with the cut on the bits the passes fixed (all of them
+  // unless the passes stopped early, when one key matches there).
   const unsigned long long cut = threshold ? cut_thr : st->prefix;
+  const unsigned long long cmask = threshold ? 0xFFFFFFFFFFFFFFFFull : st->mask;
   const uint32_t t0 = blockIdx.x * kTile;
   unsigned int less = 0, eq = 0;
 #pragma unroll 4
@@ -210,8 +237,11 @@ __global__ void __launch_bounds__(kTileThreads) select_count(const double* __res
     const uint32_t i = t0 + q * kTileThreads + threadIdx.x;  // coalesced
     if (i < n) {
       const unsigned long long key = dist_key(__ldg(dist + i));
-      less += key < cut;
-      eq += key == cut;
+      less += (key & cmask) < cut;
+      if ((key & cmask) == cut) {
+        ++eq;
+        if (cmask != 0xFFFFFFFFFFFFFFFFull) st->cut = key;  // the one matching key
+      }
     }
   }
   less = __reduce_add_sync(0xFFFFFFFFu, less);
@@ -272,7 +302,8 @@ __global__ void __launch_bounds__(kTileThreads) select_scan(
   if (threadIdx.x == 0) {
     st->n_acc = carry_acc;
     *n_acc_out = carry_acc;
-    if (eps_out) *eps_out = threshold ? eps_thr : key_to_double(st->prefix);
+    if (eps_out)
+      *eps_out = threshold ? eps_thr : key_to_double(st->mask == 0xFFFFFFFFFFFFFFFFull ? st->prefix : st->cut);
   }
 }
 
@@ -289,17 +320,19 @@ __global__ void __launch_bounds__(kTileThreads) select_write(
   __shared__ double red[3][kTileThreads / 32];
   __shared__ double s_mean[3];
   const unsigned long long cut = threshold ? cut_thr : st->prefix;
+  const unsigned long long cmask = threshold ? 0xFFFFFFFFFFFFFFFFull : st->mask;
   const unsigned long long krem = threshold ? 0xFFFFFFFFFFFFFFFFull : st->krem;
   const uint32_t t0 = blockIdx.x * kTile + threadIdx.x * kPerThread;  // contiguous per thread
   // pass 1: flags and per-thread counts
   unsigned int flags = 0, eqmask = 0, my_eq = 0;
+  unsigned long long key[kPerThread];  // all loads in flight before the compares
+#pragma unroll
+  for (int q = 0; q < kPerThread; ++q) key[q] = t0 + q < n ? dist_key(__ldg(dist + t0 + q)) : 0ull;
 #pragma unroll
   for (int q = 0; q < kPerThread; ++q) {
-    const uint32_t i = t0 + q;
-    if (i < n) {
-      const unsigned long long key = dist_key(dist[i]);
-      if (key < cut) flags |= 1u << q;
-      if (key == cut) {
+    if (t0 + q < n) {
+      if ((key[q] & cmask) < cut) flags |= 1u << q;
+      if ((key[q] & cmask) == cut) {
         eqmask |= 1u << q;
         ++my_eq;
       }
@@ -351,12 +384,17 @@ __global__ void __launch_bounds__(kTileThreads) select_write(
       }
     }
   }
-  // tile mean (fixed-order reduction), then M2 about it
+  // tile mean (fixed-order reduction), then M2 about it; a warp without an
+  // accepted sample contributes zeros without its binary64 shuffles (the
+  // same sums: its shuffle tree would add zeros only).
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool warp_any = __any_sync(0xFFFFFFFFu, flags != 0u);
   for (int d = 0; d < 3; ++d) {
     double v = sum[d];
+    if (warp_any) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    }
     if (lane == 0) red[d][warp] = v;
   }
   __syncthreads();
@@ -378,8 +416,10 @@ __global__ void __launch_bounds__(kTileThreads) select_write(
   }
   for (int d = 0; d < 3; ++d) {
     double v = m2[d];
+    if (warp_any) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    }
     if (lane == 0) red[d][warp] = v;
   }
   __syncthreads();
@@ -462,43 +502,82 @@ __global__ void __launch_bounds__(kTileThreads) select_moments(const MomentPart*
   }
 }
 
-// Posterior mean and variance from the per-thread double-float sums of
-// (theta - c) and (theta - c)^2 about a shift c (the first accepted theta):
-// a fixed-order warp shuffle tree, then the warps in order in thread 0;
-// mean = c + S1 / k and M2 = S2 - S1^2 / k in binary64.  Everything before
-// the last step runs on the binary32 pipes (a one-CTA binary64 reduction
-// would queue on this GPU's narrow FP64 pipe).  s_S1, s_S2 hold one value
-// per warp and dimension; the result is written by thread 0.
+// a / b for a double-float a and a binary32 b != 0: the binary32 quotient of
+// the leading parts, corrected once by the residual a - q b (relative error
+// about 2^-46).
+__device__ __forceinline__ DF df_div_f(DF a, float b) {
+  const float q1 = __fdiv_rn(a.hi, b);
+  const DF r = df_add(a, df_neg(df_two_prod(q1, b)));
+  return df_fast_two_sum(q1, __fdiv_rn(r.hi, b));
+}
+
+// Posterior mean and variance from double-float sums of (theta - c_w) and
+// (theta - c_w)^2 about a shift c_w per warp (its first accepted theta; nw
+// accepted samples): a fixed-order shuffle tree in each warp with any, then
+// warp 0 moves each warp's sums to the common shift c (the first accepted
+// theta overall, s_c0) -- with d = c_w - c exact as a two-sum,
+//   sum (theta - c) = S1 + nw d,   sum (theta - c)^2 = S2 + d (S1 + sum (theta - c)),
+// -- and sums them over the warps with the same tree; lane d of warp 0
+// finishes dimension d: mean = c + S1 / k and M2 = S2 - S1 (S1 / k), both in
+// double-float.  Everything runs on the binary32 pipes (a one-CTA binary64
+// reduction would queue on this GPU's narrow FP64 pipe, which a chain of
+// binary64 divisions there did), and the trees are rolled loops: this one-CTA kernel runs each instruction
+// once, so its time follows its code size.  s_S1, s_S2, s_cw hold one value
+// per warp and dimension, s_nw one count per warp (kWarps <= 32).
 template <int kWarps>
-__device__ __forceinline__ void finish_moments(DF (&S1)[3], DF (&S2)[3], const float (&c)[3],
+__device__ __forceinline__ void finish_moments(DF (&S1)[3], DF (&S2)[3], const float (&cw)[3], unsigned int nw,
                                                unsigned long long k, DF (*s_S1)[kWarps], DF (*s_S2)[kWarps],
-                                               double* post_out) {
+                                               float (*s_cw)[kWarps], const unsigned int* s_nw,
+                                               const float* s_c0, double* post_out) {
+  static_assert(kWarps <= 32, "one warp sums the warps' partial sums");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-#pragma unroll
+  if (nw != 0u) {  // warp-uniform: the sums of a warp without accepted samples are zero
+#pragma unroll 1
     for (int o = 16; o > 0; o >>= 1) {
-      S1[d] = df_add(S1[d], DF{__shfl_xor_sync(0xFFFFFFFFu, S1[d].hi, o), __shfl_xor_sync(0xFFFFFFFFu, S1[d].lo, o)});
-      S2[d] = df_add(S2[d], DF{__shfl_xor_sync(0xFFFFFFFFu, S2[d].hi, o), __shfl_xor_sync(0xFFFFFFFFu, S2[d].lo, o)});
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        S1[d] = df_add(S1[d], DF{__shfl_xor_sync(0xFFFFFFFFu, S1[d].hi, o), __shfl_xor_sync(0xFFFFFFFFu, S1[d].lo, o)});
+        S2[d] = df_add(S2[d], DF{__shfl_xor_sync(0xFFFFFFFFu, S2[d].hi, o), __shfl_xor_sync(0xFFFFFFFFu, S2[d].lo, o)});
+      }
     }
-    if (lane == 0) {
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
       s_S1[d][warp] = S1[d];
       s_S2[d][warp] = S2[d];
+      s_cw[d][warp] = cw[d];
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0 && post_out) {
-    const double kk = static_cast<double>(k);
-    for (int d = 0; d < 3; ++d) {
-      DF a = DF{0.0f, 0.0f}, b = DF{0.0f, 0.0f};
-      for (int w = 0; w < kWarps; ++w) {
-        a = df_add(a, s_S1[d][w]);
-        b = df_add(b, s_S2[d][w]);
-      }
-      const double s1 = df_to_double(a), s2 = df_to_double(b);
-      post_out[d] = k > 0 ? static_cast<double>(c[d]) + s1 / kk : nan("");
-      post_out[3 + d] = k > 1 ? (s2 - s1 * s1 / kk) / (kk - 1.0) : nan("");
+  if (warp != 0) return;
+  const unsigned int n_w = lane < kWarps ? s_nw[lane] : 0u;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    S1[d] = DF{0.0f, 0.0f};
+    S2[d] = DF{0.0f, 0.0f};
+    if (n_w != 0u) {
+      const DF a = s_S1[d][lane], b = s_S2[d][lane];
+      const DF dlt = df_two_sum(s_cw[d][lane], -s_c0[d]);
+      S1[d] = df_add(a, df_mul_f(dlt, static_cast<float>(n_w)));
+      S2[d] = df_add(b, df_mul(dlt, df_add(a, S1[d])));
     }
+  }
+#pragma unroll 1
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      S1[d] = df_add(S1[d], DF{__shfl_xor_sync(0xFFFFFFFFu, S1[d].hi, o), __shfl_xor_sync(0xFFFFFFFFu, S1[d].lo, o)});
+      S2[d] = df_add(S2[d], DF{__shfl_xor_sync(0xFFFFFFFFu, S2[d].hi, o), __shfl_xor_sync(0xFFFFFFFFu, S2[d].lo, o)});
+    }
+  }
+  if (lane < 3 && post_out) {
+    const DF a = lane == 0 ? S1[0] : (lane == 1 ? S1[1] : S1[2]);
+    const DF b = lane == 0 ? S2[0] : (lane == 1 ? S2[1] : S2[2]);
+    const float kf = static_cast<float>(k);  // exact: k <= 2^24
+    const DF m = df_div_f(a, kf);           // S1 / k
+    post_out[lane] = k > 0 ? df_to_double(df_add_f(m, s_c0[lane])) : nan("");
+    post_out[3 + lane] = k > 1 ? df_to_double(df_div_f(df_add(b, df_neg(df_mul(a, m))), kf - 1.0f)) : nan("");
   }
 }
 
@@ -515,35 +594,75 @@ __device__ __forceinline__ void add_moment(DF (&S1)[3], DF (&S2)[3], const float
 
 
 // ---------------------------------------------------------------------------
-// Up to kMidMax distances: the whole selection in one CTA, reading the
-// distances from global memory (L2) on every pass.  The
-// radix select of the large path (six 11-bit passes with warp-aggregated
-// shared histograms) runs in the CTA; the compaction walks the indices in
-// rounds of 16 per thread, carrying the equal-key rank and the output
-// position from round to round; the moments are double-float sums about the
+// Up to kMidMax distances: the whole selection in one CTA and one launch.
+// The keys are read once into shared memory (a one-CTA kernel is bound by
+// how many L2 reads one SM keeps in flight, so a pass over shared memory is
+// several times cheaper than one over L2).  The radix select of the large
+// path (up to six 11-bit passes, ending once a single key is left under the
+// prefix) runs over them; the compaction gives each warp 32 consecutive
+// indices per step, so ranks in index order come from ballots and one
+// scan over the warps' counts; the moments are double-float sums about the
 // first accepted theta (binary32 pipes: a one-CTA binary64 reduction would
-// queue on this GPU's narrow FP64 pipe).  One launch instead of eleven.
+// queue on this GPU's narrow FP64 pipe).
 // ---------------------------------------------------------------------------
 constexpr int kMidThreads = 1024;
-constexpr uint32_t kMidMax = 24576;  // above this the multi-CTA passes are faster
-constexpr int kMidPer = 16;
-constexpr uint32_t kMidRound = kMidThreads * kMidPer;
+constexpr int kMidWarps = kMidThreads / 32;
+constexpr uint32_t kMidMax = 24576;  // keys in shared memory: 192 KB
+constexpr int kMidChunk = 8;         // loads in flight per thread
+constexpr uint32_t kMidList = kBins;  // accepted indices listed in the histogram's shared memory
+constexpr size_t kMidKeyBytes = static_cast<size_t>(kMidMax) * sizeof(unsigned long long);
+
+// Exclusive prefix over the warps of one value per warp (v[w], kMidWarps =
+// 32 of them), computed by every warp for itself; *all = the sum.
+__device__ __forceinline__ unsigned int warp_base_of(const unsigned int* v, int warp, unsigned int* all) {
+  const int lane = threadIdx.x & 31;
+  const unsigned int x0 = v[lane];
+  unsigned int x = x0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  *all = __shfl_sync(0xFFFFFFFFu, x, 31);
+  return __shfl_sync(0xFFFFFFFFu, x - x0, warp);
+}
 
 template <bool kTheta>
-__global__ void __launch_bounds__(kMidThreads) select_mid(
+__global__ void __launch_bounds__(kMidThreads, 1) select_mid(
     const double* __restrict__ dist, uint32_t n, unsigned long long k, bool threshold,
     unsigned long long cut_thr, double eps_thr, const __grid_constant__ OUConst prm, uint32_t base,
     const float* __restrict__ theta, uint32_t* __restrict__ idx_out, float4* __restrict__ rec_out,
     unsigned long long cap, unsigned long long* __restrict__ n_acc_out, double* __restrict__ eps_out,
     double* __restrict__ post_out) {
+  extern __shared__ unsigned long long s_raw[];  // the n distances' bit patterns
   __shared__ unsigned int h[kBins];
-  __shared__ unsigned int scan_smem[kMidThreads / 32];
-  __shared__ unsigned long long scan64[kMidThreads / 32];
-  __shared__ unsigned long long s_prefix, s_mask, s_krem;
-  __shared__ unsigned int acc_bits[kMidMax / 32];
+  __shared__ unsigned int scan_smem[kMidWarps];
+  __shared__ unsigned long long s_prefix, s_mask, s_krem, s_cut;
+  __shared__ unsigned int s_bin_count;
+  __shared__ unsigned int acc_bits[kMidMax / 32];  // bit (i & 31) of word i >> 5: index i accepted
+  __shared__ unsigned int s_weq[kMidWarps], s_wacc[kMidWarps];
   __shared__ float s_shift[3];
-  __shared__ DF s_S1[3][kMidThreads / 32], s_S2[3][kMidThreads / 32];
-  const int lane = threadIdx.x & 31;
+  __shared__ DF s_S1[3][kMidWarps], s_S2[3][kMidWarps];
+  __shared__ float s_cw[3][kMidWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned int lane_lt = (1u << lane) - 1u;
+  // 0. The distances into shared memory, kMidChunk loads in flight per
+  // thread; their keys are formed where they are read.
+  const unsigned long long* __restrict__ dbits = reinterpret_cast<const unsigned long long*>(dist);
+  for (uint32_t i0 = 0; i0 < n; i0 += kMidThreads * kMidChunk) {
+    unsigned long long t[kMidChunk];
+#pragma unroll
+    for (int j = 0; j < kMidChunk; ++j) {
+      const uint32_t i = i0 + j * kMidThreads + threadIdx.x;
+      t[j] = i < n ? __ldg(dbits + i) : 0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < kMidChunk; ++j) {
+      const uint32_t i = i0 + j * kMidThreads + threadIdx.x;
+      if (i < n) s_raw[i] = t[j];
+    }
+  }
+  __syncthreads();
   unsigned long long prefix = 0ull, mask = 0ull, krem = k;
   // 1. Radix select of the k-th smallest key (skipped in threshold mode).
   if (!threshold) {
@@ -552,15 +671,9 @@ __global__ void __launch_bounds__(kMidThreads) select_mid(
       const unsigned long long dmask = (1ull << kPassBits[pass]) - 1ull;
       for (int b = threadIdx.x; b < kBins; b += kMidThreads) h[b] = 0u;
       __syncthreads();
-      for (uint32_t b0 = 0; b0 < n; b0 += kMidThreads) {  // uniform bound: every lane reaches the match
-        const uint32_t i = b0 + threadIdx.x;
-        unsigned int bin = 0xFFFFFFFFu;
-        if (i < n) {
-          const unsigned long long key = dist_key(__ldg(dist + i));
-          if ((key & mask) == prefix) bin = static_cast<unsigned int>((key >> shift) & dmask);
-        }
-        const unsigned int peers = __match_any_sync(0xFFFFFFFFu, bin);
-        if (bin != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&h[bin], __popc(peers));
+      for (uint32_t i = threadIdx.x; i < n; i += kMidThreads) {
+        const unsigned long long key = key_of_bits(s_raw[i]);
+        if ((key & mask) == prefix) atomicAdd(&h[static_cast<unsigned int>((key >> shift) & dmask)], 1u);
       }
       __syncthreads();
       constexpr int kPer = kBins / kMidThreads;  // bins owned by one thread
@@ -581,6 +694,7 @@ __global__ void __launch_bounds__(kMidThreads) select_mid(
             s_prefix = prefix | (static_cast<unsigned long long>(threadIdx.x * kPer + q) << shift);
             s_mask = mask | (dmask << shift);
             s_krem = krem - run;
+            s_bin_count = c[q];
           }
           run += c[q];
         }
@@ -589,108 +703,157 @@ __global__ void __launch_bounds__(kMidThreads) select_mid(
       prefix = s_prefix;
       mask = s_mask;
       krem = s_krem;
+      // One key left under the prefix: it is the k-th smallest, and the bits
+      // fixed so far order every other key against it.
+      if (s_bin_count == 1u) break;
     }
   }
+  // Keys compare with the cut on the bits the passes fixed (all of them when
+  // the passes ran out, as with ties); every key equal to the cut there has
+  // the cut's full value (one such key if the passes stopped early), which
+  // gives epsilon.
   const unsigned long long cut = threshold ? cut_thr : prefix;
+  const unsigned long long cmask = threshold ? 0xFFFFFFFFFFFFFFFFull : mask;
   if (threshold) krem = 0xFFFFFFFFFFFFFFFFull;
-  // 2. Compaction in index order, 16 consecutive indices per thread and round;
-  // the accepted indices are also marked in a bit set for the moments.
-  for (uint32_t w = threadIdx.x; w < kMidMax / 32; w += kMidThreads) acc_bits[w] = 0u;
+  // 2. Compaction in index order: warp w takes the block [g0, g1) of
+  // consecutive indices, 32 at a time (lane = index - g).  Where the keys
+  // equal to the cut are split by the rank (ties across the k-th), one scan
+  // over the warps gives their ranks; a second gives the output positions.
   if (threadIdx.x < 3) s_shift[threadIdx.x] = 0.0f;
-  __syncthreads();
-  unsigned long long carry_eq = 0ull, carry_acc = 0ull;
-  for (uint32_t rb = 0; rb < n; rb += kMidRound) {
-    const uint32_t t0 = rb + threadIdx.x * kMidPer;
-    unsigned int flags = 0, eqmask = 0, my_eq = 0;
-#pragma unroll
-    for (int q = 0; q < kMidPer; ++q) {
-      const uint32_t i = t0 + q;
-      if (i < n) {
-        const unsigned long long key = dist_key(dist[i]);
-        if (key < cut) flags |= 1u << q;
-        if (key == cut) {
-          eqmask |= 1u << q;
-          ++my_eq;
-        }
-      }
+  const uint32_t span = (n + kMidThreads - 1) / kMidThreads * 32u;  // a multiple of 32
+  const uint32_t g0 = min(n, warp * span), g1 = min(n, g0 + span);  // warp-uniform
+  const bool rank_eq = !threshold && krem < s_bin_count;            // CTA-uniform
+  unsigned long long eq_rank = 0ull;  // equal keys before this warp's block
+  if (rank_eq) {
+    unsigned int weq = 0;
+    for (uint32_t g = g0; g < g1; g += 32u) {
+      const uint32_t i = g + lane;
+      weq += __popc(__ballot_sync(0xFFFFFFFFu, i < n && (key_of_bits(s_raw[i]) & cmask) == cut));
     }
-    unsigned long long tot_eq;
-    const unsigned long long eq_rank0 =
-        carry_eq + block_exclusive_scan<unsigned long long>(my_eq, &tot_eq, scan64);
-    {
-      unsigned long long r = eq_rank0;
-#pragma unroll
-      for (int q = 0; q < kMidPer; ++q) {
-        if (eqmask & (1u << q)) {
-          if (r < krem) flags |= 1u << q;
-          ++r;
-        }
-      }
-    }
-    unsigned long long tot_acc;
-    unsigned long long pos =
-        carry_acc + block_exclusive_scan<unsigned long long>(__popc(flags), &tot_acc, scan64);
-    // 16 indices starting at a multiple of 16: half of one bit-set word
-    if (flags) atomicOr(&acc_bits[t0 >> 5], flags << (t0 & 16u));
-#pragma unroll
-    for (int q = 0; q < kMidPer; ++q) {
-      if (flags & (1u << q)) {
-        const uint32_t i = t0 + q;
-        float th[3];
-        if (kTheta) {
-          th[0] = theta[i];
-          th[1] = theta[static_cast<size_t>(n) + i];
-          th[2] = theta[2 * static_cast<size_t>(n) + i];
-        } else {
-          ou_prior(prm, base + i, th[0], th[1], th[2]);
-        }
-        if (pos == 0) {
-          s_shift[0] = th[0];
-          s_shift[1] = th[1];
-          s_shift[2] = th[2];
-        }
-        if (pos < cap) {
-          idx_out[pos] = i;
-          rec_out[pos] = make_float4(th[0], th[1], th[2], static_cast<float>(dist[i]));
-        }
-        ++pos;
-      }
-    }
-    carry_eq += tot_eq;
-    carry_acc += tot_acc;
+    if (lane == 0) s_weq[warp] = weq;
+    __syncthreads();
+    unsigned int tot_eq;
+    eq_rank = warp_base_of(s_weq, warp, &tot_eq);
   }
+  unsigned int wacc = 0;
+  for (uint32_t g = g0; g < g1; g += 32u) {
+    const uint32_t i = g + lane;
+    const unsigned long long full = i < n ? key_of_bits(s_raw[i]) : 0ull;
+    const unsigned long long key = full & cmask;
+    const bool less = i < n && key < cut;
+    const bool eq = i < n && key == cut;
+    if (eq) s_cut = full;
+    const unsigned int eqb = __ballot_sync(0xFFFFFFFFu, eq);
+    const bool take_eq = eq && (!rank_eq || eq_rank + __popc(eqb & lane_lt) < krem);
+    const unsigned int accb = __ballot_sync(0xFFFFFFFFu, less || take_eq);
+    if (lane == 0) acc_bits[g >> 5] = accb;
+    eq_rank += __popc(eqb);
+    wacc += __popc(accb);
+  }
+  if (lane == 0) s_wacc[warp] = wacc;
   __syncthreads();
-  // 3. Moments about the first accepted theta c: the sums of (theta - c) and
-  // (theta - c)^2 in double-float (each difference exact as a two-sum), per
-  // thread in index order, then a fixed-order tree over the CTA;
-  // mean = c + S1 / k and M2 = S2 - S1^2 / k in binary64.  The accepted theta
-  // are formed again from their counters (or read again).
-  const float cs[3] = {s_shift[0], s_shift[1], s_shift[2]};
+  // 3. Output in index order, and the moments: each thread sums (theta - c_w)
+  // and (theta - c_w)^2 in double-float (each difference exact as a
+  // two-sum) about its warp's first accepted theta c_w; the warps' sums are
+  // moved to the first accepted theta overall and added in a fixed order.
+  unsigned int n_acc;
+  unsigned long long pos = warp_base_of(s_wacc, warp, &n_acc);  // accepted before this warp's
+  float cw[3] = {0.0f, 0.0f, 0.0f};
+  bool have_cw = false;  // warp-uniform
   DF S1[3] = {DF{0.0f, 0.0f}, DF{0.0f, 0.0f}, DF{0.0f, 0.0f}};
   DF S2[3] = {DF{0.0f, 0.0f}, DF{0.0f, 0.0f}, DF{0.0f, 0.0f}};
-  for (uint32_t rb = 0; rb < n; rb += kMidRound) {
-    const uint32_t t0 = rb + threadIdx.x * kMidPer;
-    const unsigned int flags = t0 < n ? (acc_bits[t0 >> 5] >> (t0 & 16u)) & 0xFFFFu : 0u;
+  // theta of accepted index i at output position p, written out; the first
+  // accepted theta overall is the moments' common shift.
+  auto emit = [&](uint32_t i, unsigned long long p, float (&th)[3]) {
+    if (kTheta) {
+      th[0] = theta[i];
+      th[1] = theta[static_cast<size_t>(n) + i];
+      th[2] = theta[2 * static_cast<size_t>(n) + i];
+    } else {
+      ou_prior(prm, base + i, th[0], th[1], th[2]);
+    }
+    if (p == 0) {
+      s_shift[0] = th[0];
+      s_shift[1] = th[1];
+      s_shift[2] = th[2];
+    }
+    if (p < cap) {
+      idx_out[p] = i;
+      rec_out[p] = make_float4(th[0], th[1], th[2], static_cast<float>(__longlong_as_double(s_raw[i])));
+    }
+  };
+  // Lane q holds the bit-set word of the warp's q-th group (at most 32
+  // groups) and the number accepted in the groups before it.
+  static_assert(kMidMax / kMidThreads <= 32, "a warp's groups fit in one word per lane");
+  const uint32_t n_groups = (g1 - g0 + 31u) / 32u;
+  const unsigned int word = static_cast<uint32_t>(lane) < n_groups ? acc_bits[(g0 >> 5) + lane] : 0u;
+  unsigned int before = __popc(word);
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, before, o);
+    if (lane >= o) before += y;
+  }
+  before -= __popc(word);
+  unsigned int busy = __ballot_sync(0xFFFFFFFFu, word != 0u);
+  unsigned int nw;  // accepted samples this warp sums
+  if (n_acc <= kMidList) {  // CTA-uniform
+    // Few accepted: their indices go to a list in output order (in the
+    // histogram's place), and then every lane takes one, so that the prior
+    // draws and the sums run on full warps.
+    unsigned int* list = h;
 #pragma unroll 1
-    for (int q = 0; q < kMidPer; ++q) {
-      if (flags & (1u << q)) {
-        const uint32_t i = t0 + q;
-        float th[3];
-        if (kTheta) {
-          th[0] = theta[i];
-          th[1] = theta[static_cast<size_t>(n) + i];
-          th[2] = theta[2 * static_cast<size_t>(n) + i];
-        } else {
-          ou_prior(prm, base + i, th[0], th[1], th[2]);
-        }
-        add_moment(S1, S2, th, cs);
+    while (busy != 0u) {  // warp-uniform
+      const int q = __ffs(busy) - 1;
+      busy &= busy - 1u;
+      const unsigned int accb = __shfl_sync(0xFFFFFFFFu, word, q);
+      const unsigned int bq = __shfl_sync(0xFFFFFFFFu, before, q);
+      if ((accb >> lane) & 1u) list[pos + bq + __popc(accb & lane_lt)] = g0 + 32u * q + lane;
+    }
+    __syncthreads();
+    unsigned int mine_count = 0;
+#pragma unroll 1
+    for (uint32_t p0 = warp * 32u; p0 < n_acc; p0 += kMidThreads) {  // warp-uniform
+      const uint32_t p = p0 + lane;
+      const bool mine = p < n_acc;
+      float th[3] = {0.0f, 0.0f, 0.0f};
+      if (mine) emit(list[p], p, th);
+      if (!have_cw) {  // lane 0 holds the warp's first sample
+#pragma unroll
+        for (int d = 0; d < 3; ++d) cw[d] = __shfl_sync(0xFFFFFFFFu, th[d], 0);
+        have_cw = true;
+      }
+      if (mine) {
+        add_moment(S1, S2, th, cw);
+        ++mine_count;
       }
     }
+    nw = __reduce_add_sync(0xFFFFFFFFu, mine_count);
+    if (lane == 0) s_wacc[warp] = nw;  // read again only by the moments
+  } else {
+    // Many accepted: the warp visits its groups that hold accepted samples.
+#pragma unroll 1
+    while (busy != 0u) {  // warp-uniform
+      const int q = __ffs(busy) - 1;
+      busy &= busy - 1u;
+      const unsigned int accb = __shfl_sync(0xFFFFFFFFu, word, q);
+      const unsigned long long pq = pos + __shfl_sync(0xFFFFFFFFu, before, q);
+      const bool mine = (accb >> lane) & 1u;
+      float th[3] = {0.0f, 0.0f, 0.0f};
+      if (mine) emit(g0 + 32u * q + lane, pq + __popc(accb & lane_lt), th);
+      if (!have_cw) {
+        const int src = __ffs(accb) - 1;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) cw[d] = __shfl_sync(0xFFFFFFFFu, th[d], src);
+        have_cw = true;
+      }
+      if (mine) add_moment(S1, S2, th, cw);
+    }
+    nw = wacc;
   }
-  finish_moments<kMidThreads / 32>(S1, S2, cs, carry_acc, s_S1, s_S2, post_out);
+  finish_moments<kMidWarps>(S1, S2, cw, nw, n_acc, s_S1, s_S2, s_cw, s_wacc, s_shift, post_out);
   if (threadIdx.x == 0) {
-    *n_acc_out = carry_acc;
-    if (eps_out) *eps_out = threshold ? eps_thr : key_to_double(cut);
+    *n_acc_out = n_acc;
+    if (eps_out) *eps_out = threshold ? eps_thr : key_to_double(s_cut);
   }
 }
 
@@ -706,23 +869,45 @@ unsigned long long host_dist_key(double d) {
 
 size_t select_workspace_bytes(uint64_t n) { return WsLayout(n).total; }
 
+// The one-CTA selection keeps up to kMidMax keys in shared memory, above the
+// default 48 KB: the limit is raised once per device (a host call, made
+// before any stream capture that launches the selection).
+cudaError_t select_prepare() {
+  static std::atomic<unsigned long long> ready{0ull};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (ready.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(select_mid<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kMidKeyBytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(select_mid<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kMidKeyBytes));
+  if (e == cudaSuccess && bit) ready.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
 cudaError_t launch_select(const double* dist, uint32_t n, uint64_t k, double eps,
                           const OUConst& P_, uint64_t base, const float* theta, uint32_t* idx_out,
                           float* rec_out, uint64_t cap, uint64_t* n_acc_out, double* eps_out,
                           double* post_out, void* ws, cudaStream_t s) {
   const bool threshold = (k == 0);
   if (n > 0 && n <= kMidMax) {
+    cudaError_t e = select_prepare();
+    if (e != cudaSuccess) return e;
     const unsigned long long cut = threshold ? host_dist_key(eps) : 0ull;
+    const size_t smem = static_cast<size_t>(n) * sizeof(unsigned long long);
     if (theta)
-      select_mid<true><<<1, kMidThreads, 0, s>>>(dist, n, k, threshold, cut, eps, P_, static_cast<uint32_t>(base),
-                                                 theta, idx_out, reinterpret_cast<float4*>(rec_out), cap,
-                                                 reinterpret_cast<unsigned long long*>(n_acc_out), eps_out,
-                                                 post_out);
+      select_mid<true><<<1, kMidThreads, smem, s>>>(dist, n, k, threshold, cut, eps, P_, static_cast<uint32_t>(base),
+                                                    theta, idx_out, reinterpret_cast<float4*>(rec_out), cap,
+                                                    reinterpret_cast<unsigned long long*>(n_acc_out), eps_out,
+                                                    post_out);
     else
-      select_mid<false><<<1, kMidThreads, 0, s>>>(dist, n, k, threshold, cut, eps, P_, static_cast<uint32_t>(base),
-                                                  theta, idx_out, reinterpret_cast<float4*>(rec_out), cap,
-                                                  reinterpret_cast<unsigned long long*>(n_acc_out), eps_out,
-                                                  post_out);
+      select_mid<false><<<1, kMidThreads, smem, s>>>(dist, n, k, threshold, cut, eps, P_, static_cast<uint32_t>(base),
+                                                     theta, idx_out, reinterpret_cast<float4*>(rec_out), cap,
+                                                     reinterpret_cast<unsigned long long*>(n_acc_out), eps_out,
+                                                     post_out);
     return cudaGetLastError();
   }
   const WsLayout L(n);

@@ -158,6 +158,15 @@ def _select_cases():
     # around the one-CTA selection's limit (24576 distances), heavy ties
     for n in (24575, 24576, 24577, 30001):
         yield f"mid{n}", np.round(rng.exponential(size=n), 1)
+    # distinct values: the radix passes stop once one key is left under the
+    # prefix (after two or three passes here) ...
+    for n in (1000, 24576, 30001):
+        yield f"distinct{n}", rng.uniform(0, 1, size=n)
+    # ... or only at the fifth (spacing 2^-43) or the last pass (2^-52), where
+    # the values differ in their low bits
+    for e in (43, 52):
+        for n in (5000, 30001):
+            yield f"lowbits{e}_{n}", 1.0 + rng.permutation(n) * 2.0 ** -e
 
 
 @pytest.mark.parametrize("case", [c for c, _ in _select_cases()])
@@ -175,6 +184,13 @@ def test_select_exact_on_given_distances(case):
         idx_o = oracle.select_topk(d, k).astype(np.int64)
         np.testing.assert_array_equal(to_np(sel["idx"]).astype(np.int64), idx_o, err_msg=f"k={k}")
         assert int(to_np(sel["n_acc"])[0]) == k
+        # epsilon is the k-th smallest distance (NaN above every number)
+        acc = d[idx_o]
+        eps_k = to_np(sel["eps"])[0]
+        if np.isnan(acc).any():
+            assert np.isnan(eps_k), f"k={k}"
+        else:
+            assert eps_k == acc.max(), f"k={k}"
         mean_o, var_o = oracle.moments(theta.T.astype(np.float64), idx_o.astype(np.uint64))
         post = to_np(sel["post"])
         np.testing.assert_allclose(post[:3], mean_o, rtol=1e-12, atol=1e-12)
