@@ -926,7 +926,9 @@ cudaError_t launch_select(const double* dist, uint32_t n, uint64_t k, double eps
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint32_t want = (n + kHistThreads * 8 - 1) / (kHistThreads * 8);
+    // one key per thread up to 8 CTAs per SM: the passes are latency-bound
+    // at the sizes where that leaves the GPU partly idle
+    const uint32_t want = (n + kHistThreads - 1) / kHistThreads;
     const uint32_t cap_blocks = static_cast<uint32_t>(sms > 0 ? sms : 1) * 8u;
     const uint32_t blocks = want < 1 ? 1 : (want > cap_blocks ? cap_blocks : want);
     for (int pass = 0; pass < kNumPasses; ++pass)
