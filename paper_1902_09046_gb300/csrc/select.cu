@@ -595,19 +595,20 @@ __device__ __forceinline__ void add_moment(DF (&S1)[3], DF (&S2)[3], const float
 
 // ---------------------------------------------------------------------------
 // Up to kMidMax distances: the whole selection in one CTA and one launch.
-// The keys are read once into shared memory (a one-CTA kernel is bound by
-// how many L2 reads one SM keeps in flight, so a pass over shared memory is
-// several times cheaper than one over L2).  The radix select of the large
-// path (up to six 11-bit passes, ending once a single key is left under the
-// prefix) runs over them; the compaction gives each warp 32 consecutive
-// indices per step, so ranks in index order come from ballots and one
-// scan over the warps' counts; the moments are double-float sums about the
-// first accepted theta (binary32 pipes: a one-CTA binary64 reduction would
-// queue on this GPU's narrow FP64 pipe).
+// The distances' bit patterns are read once into shared memory (a one-CTA
+// kernel is bound by how many L2 reads one SM keeps in flight, so a pass
+// over shared memory is several times cheaper than one over L2).  The radix
+// select of the large path (up to six 11-bit passes, ending once a single
+// key is left under the prefix) runs over them; the compaction gives each
+// warp a block of consecutive indices, 32 at a time, so ranks in index order
+// come from ballots and one scan over the warps' counts; with few accepted,
+// their indices are listed first and then taken one per lane; the moments
+// are double-float sums about per-warp shifts (binary32 pipes: a one-CTA
+// binary64 reduction would queue on this GPU's narrow FP64 pipe).
 // ---------------------------------------------------------------------------
 constexpr int kMidThreads = 1024;
 constexpr int kMidWarps = kMidThreads / 32;
-constexpr uint32_t kMidMax = 24576;  // keys in shared memory: 192 KB
+constexpr uint32_t kMidMax = 24576;  // bit patterns in shared memory: 192 KB
 constexpr int kMidChunk = 8;         // loads in flight per thread
 constexpr uint32_t kMidList = kBins;  // accepted indices listed in the histogram's shared memory
 constexpr size_t kMidKeyBytes = static_cast<size_t>(kMidMax) * sizeof(unsigned long long);
@@ -869,7 +870,7 @@ unsigned long long host_dist_key(double d) {
 
 size_t select_workspace_bytes(uint64_t n) { return WsLayout(n).total; }
 
-// The one-CTA selection keeps up to kMidMax keys in shared memory, above the
+// The one-CTA selection keeps up to kMidMax distances in shared memory, above the
 // default 48 KB: the limit is raised once per device (a host call, made
 // before any stream capture that launches the selection).
 cudaError_t select_prepare() {
