@@ -615,6 +615,7 @@ constexpr size_t kMidKeyBytes = static_cast<size_t>(kMidMax) * sizeof(unsigned l
 
 // Exclusive prefix over the warps of one value per warp (v[w], kMidWarps =
 // 32 of them), computed by every warp for itself; *all = the sum.
+static_assert(kMidWarps == 32, "one lane per warp of the CTA");
 __device__ __forceinline__ unsigned int warp_base_of(const unsigned int* v, int warp, unsigned int* all) {
   const int lane = threadIdx.x & 31;
   const unsigned int x0 = v[lane];
