@@ -674,7 +674,7 @@ BEGE_SOURCES = ("paper_1902_09046_gb300/csrc/bege.cu", "paper_1902_09046_gb300/c
 
 
 def bege_mode(args):
-    """BEGE log-likelihoods (Sec. 4.3) of 1024 particles on a 1099-month
+    """BEGE log-likelihoods (Sec. 4.2) of 1024 particles on a 1099-month
     return series, as in one SMC iteration of the paper's BEGE inference:
     particle-months per second, for particles drawn from the prior (the first
     iteration) and particles concentrated around a plausible parameter vector

@@ -514,7 +514,7 @@ int weakinf_test(const double *lambda, uint32_t n_lambda, double lambda0, uint32
 #define PPABC_BEGE_MAX_T (1 << 16)
 
 /*
- * BEGE log-likelihood (Sec. 4.3: the BEGE model of monthly return
+ * BEGE log-likelihood (Sec. 4.2: the BEGE model of monthly return
  * innovations, its shape recursion, Eq. BEGE_LL, the distribution function
  * Eq. CDF_BEGE discretised as Eq. BEGE_LL_approx, P(a, x) of Eq. incompGamma)
  * for n_particles parameter vectors on one return series r_1..r_T.

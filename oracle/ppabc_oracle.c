@@ -762,7 +762,7 @@ int orc_recalibrate(const double *summ, const float *theta, uint64_t n, uint32_t
 }
 
 /* ---------------------------------------------------------------------------
- * BEGE log-likelihood (Sec. 4.3: the BEGE model, its shape recursion, the
+ * BEGE log-likelihood (Sec. 4.2: the BEGE model, its shape recursion, the
  * log-likelihood Eq. BEGE_LL, the distribution function Eq. CDF_BEGE
  * discretised as Eq. BEGE_LL_approx, and P(a, x) of Eq. incompGamma).
  * ------------------------------------------------------------------------- */
@@ -838,7 +838,7 @@ double orc_bege_cdf(double u, double sp, double sn, double p, double n) {
 }
 
 /* The BEGE density by central finite differences of the distribution
- * function (Sec. 4.3: density from the distribution function by finite
+ * function (Sec. 4.2: density from the distribution function by finite
  * differences), step h. */
 double orc_bege_density(double u, double sp, double sn, double p, double n, double h) {
   return (orc_bege_cdf(u + h, sp, sn, p, n) - orc_bege_cdf(u - h, sp, sn, p, n)) / (2.0 * h);

@@ -141,7 +141,7 @@ int orc_recalibrate(const double *summ, const float *theta, uint64_t n, uint32_t
                     const uint32_t *acc, uint64_t q, uint64_t k, double *u, float *theta_rc,
                     int n_threads);
 
-/* BEGE log-likelihood (Sec. 4.3).  theta is [ORC_BEGE_NPAR][np] (row k =
+/* BEGE log-likelihood (Sec. 4.2).  theta is [ORC_BEGE_NPAR][np] (row k =
  * parameter k of every particle) in the order (p0, sigma_p, rho_p, phi_p+,
  * phi_p-, n0, sigma_n, rho_n, phi_n+, phi_n-, mu); r holds r_1..r_T; the
  * density is the central difference of the discretised distribution function

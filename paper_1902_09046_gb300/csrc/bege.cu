@@ -1,5 +1,5 @@
 // bege.cu -- BEGE log-likelihood of many parameter vectors on one return
-// series (Sec. 4.3: the BEGE model, its shape recursion, Eq. BEGE_LL,
+// series (Sec. 4.2: the BEGE model, its shape recursion, Eq. BEGE_LL,
 // Eq. CDF_BEGE discretised as Eq. BEGE_LL_approx, P(a, x) of Eq. incompGamma).
 //
 // For particle i with theta = (p0, sp, rho_p, phi_p+, phi_p-, n0, sn, rho_n,

@@ -207,7 +207,7 @@ def toggle_observed_quantiles(seed: int = 7) -> np.ndarray:
     return loc + 100.0 * stats.lognorm.ppf(levels, s=scale)
 
 
-# BEGE model (Sec. 4.3): parameter order and the paper's uniform prior box
+# BEGE model (Sec. 4.2): parameter order and the paper's uniform prior box
 # (p0, sigma_p, rho_p, phi_p+, phi_p-, n0, sigma_n, rho_n, phi_n+, phi_n-, mu).
 BEGE_PARAMS = ("p0", "sigma_p", "rho_p", "phi_p_plus", "phi_p_minus",
                "n0", "sigma_n", "rho_n", "phi_n_plus", "phi_n_minus", "mu")

@@ -1,4 +1,4 @@
-"""Pins of the oracle's BEGE log-likelihood (Sec. 4.3) to facts other than
+"""Pins of the oracle's BEGE log-likelihood (Sec. 4.2) to facts other than
 its own code: scipy's incomplete gamma and closed forms, the limits of the
 discretised distribution function, a Monte Carlo estimate of the integral
 it discretises, the analytic derivative of that sum, and shape recursions
