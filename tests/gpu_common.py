@@ -33,6 +33,29 @@ DIST_RTOL = 1e-5
 BAND = 1e-6
 
 
+def posterior_bounds(th_gpu, th_orc, idx):
+    """Bounds on the posterior mean and variance differences over one index
+    set when the two sides hold the same samples up to the per-element
+    difference delta_i = theta_gpu,i - theta_orc,i (|delta_i| <= d).
+
+    mean: |dm| <= max |delta_i| = d (a mean of the delta_i).
+    var: with a_i = theta_i - m and e_i = delta_i - mean(delta), the centred
+    sums differ by 2 sum a_i e_i + sum e_i^2 = 2 sum a_i delta_i + sum e_i^2
+    (sum a_i = 0), so (k - 1) |dv| <= 2 d sum |a_i| + k d^2
+    <= 2 d sqrt(k (k - 1) v) + k d^2 (Cauchy-Schwarz).
+    A rounding allowance of 1e-12 relative is added to each (binary64 and
+    double-float reductions).  Returns (mean_tol[3], var_tol[3], d[3])."""
+    idx = np.asarray(idx, dtype=np.int64)
+    k = idx.size
+    a, b = th_gpu[idx].astype(np.float64), th_orc[idx].astype(np.float64)
+    d = np.abs(a - b).max(axis=0)
+    m = b.mean(axis=0)
+    v = b.var(axis=0, ddof=1) if k > 1 else np.full(3, np.nan)
+    mean_tol = d + 1e-12 * (np.abs(m) + 1e-300)
+    var_tol = (2 * d * np.sqrt(k * (k - 1) * v) + k * d ** 2) / max(k - 1, 1) + 1e-12 * v
+    return mean_tol, var_tol, d
+
+
 def band_check(idx_gpu, idx_orc, d_orc, eps_orc, band=BAND):
     """Every index in exactly one of the two accept sets lies within the band
     around epsilon (computed from the oracle's distances); returns the number

@@ -34,11 +34,16 @@ def test_sweep_parity(n_obs, M):
     assert np.all(err <= ybar_tol(lams))
     # the GPU count is exactly its own indicator sum
     np.testing.assert_array_equal(c_g, (np.abs(y_g) >= abs(ybar_obs)).sum(axis=1))
-    # indicators agree with the oracle outside the band
+    # indicators agree with the oracle outside the band, which is set per
+    # lambda from the stated ybar error: a data set can change side only if
+    # | |ybar| - |ybar_obs| | is below the largest error the two sides can
+    # have, so band_k = max(BAND |ybar_obs|, 2 ybar_tol(lambda_k))
     a = abs(ybar_obs)
-    outside = np.abs(np.abs(y_o) - a) >= BAND * a
+    band_w = np.maximum(BAND * a, 2.0 * ybar_tol(lams))
+    outside = np.abs(np.abs(y_o) - a) >= band_w
     np.testing.assert_array_equal((np.abs(y_g) >= a)[outside], (np.abs(y_o) >= a)[outside])
     band = (~outside).sum(axis=1)
+    print(f"n={n_obs} M={M}: data sets inside the band per lambda {band.tolist()}")
     assert np.all(np.abs(c_g - c_o.astype(np.int64)) <= band)
     np.testing.assert_array_equal(p_g, c_g / M)
 

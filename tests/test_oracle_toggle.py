@@ -7,6 +7,12 @@
   fixed in closed form.
 * The coupling direction: a large v represses u (p_u = v^beta_u), a v held
   at the floor does not.
+* The floor at 1 (the C listing of Sec. 3.4 clamps u and v after each
+  update): with alpha_u = alpha_v = -1000 and beta = 0 every unclamped update
+  lands below -400 whatever the normal (|zeta| <= 5.77 for this generator), so
+  u = v = 1 exactly after every step, and y = 1 + mu + mu sigma eta is
+  N(1 + mu, (mu sigma)^2) for any gamma.  Without the clamp u would end near
+  -1.7e4; a clamp at 0, or one applied before the update, ends elsewhere.
 * The 19 summaries are numpy's linear-interpolation quantiles of the cells'
   y values, rho is their Euclidean distance to the observed ones, y >= 1,
   and the prior draws are uniform on the paper's box.
@@ -74,6 +80,19 @@ def test_linear_regime_observation_noise():
     N = y.size
     assert abs(y.mean() - (mean_u + mu)) < Z * np.sqrt(var_y / N)
     assert abs(y.var() - var_y) < Z * var_y * np.sqrt(2.0 / N), (y.var(), var_y)
+
+
+def test_clamp_holds_both_states_at_the_floor():
+    mu, sigma, gam = 300.0, 0.05, 0.7
+    T, C, n = 40, 8000, 2
+    m = fixed((mu, sigma, gam, -1000.0, -1000.0, 0.0, 0.0), T, C)
+    _, _, y, _, uv = oracle.toggle_prior_predictive(m, np.zeros(19), n, seed=12, want_y=True, want_uv=True)
+    assert np.all(uv == 1.0)
+    y = y.ravel()
+    sd = mu * sigma
+    N = y.size
+    assert abs(y.mean() - (1.0 + mu)) < Z * sd / np.sqrt(N), y.mean()
+    assert abs(y.var() - sd ** 2) < Z * sd ** 2 * np.sqrt(2.0 / N), (y.var(), sd ** 2)
 
 
 def test_v_represses_u():
