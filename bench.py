@@ -41,7 +41,8 @@ SM_MAX_MHZ = 2070.0
 MUFU_PER_SM_CLK = 16          # special-function (MUFU) lanes per SM per clock
 MUFU_PER_PATH_STEP = 2.0      # log, sqrt, sin, cos per Box-Muller pair = 2 per normal
 KERNEL_SOURCES = ("paper_1902_09046_gb300/csrc/em_ou.cu", "paper_1902_09046_gb300/csrc/ou_path.cuh",
-                  "paper_1902_09046_gb300/csrc/rng.cuh")
+                  "paper_1902_09046_gb300/csrc/rng.cuh", "paper_1902_09046_gb300/csrc/bm_table.cuh",
+                  "paper_1902_09046_gb300/csrc/bm_tables.h")
 
 
 def parse_args():
@@ -246,7 +247,7 @@ def profiled_traffic(n_samples):
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    if rec.get("source_hash") != kernel_source_hash():
+    if rec.get("source_hash") != kernel_source_hash() or rec.get("dram_bytes") is None:
         return None
     return float(rec["dram_bytes"]) * n_samples / float(rec["n_samples"])
 

@@ -34,9 +34,10 @@
  *     There is no CPU fallback.
  *
  * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = (seed low 32
- * bits, seed high 32 bits), counter = (c0 block, c1 sample / data-set index,
- * c2 substream, c3 tag) with tag 0 for prior draws and 1 for path / data
- * normals.  A 32-bit word w encodes the uniform ((w >> 9) + 1/2) 2^-23 and
+ * bits, seed high 32 bits).  Block b of the stream (index, substream, tag)
+ * is counter (c0, c1, c2, c3) = (tag, b, substream, index), with tag 0 for
+ * prior draws (block 0) and 1 for path / data normals; the index is the
+ * global sample or data-set index.  A 32-bit word w encodes the uniform ((w >> 9) + 1/2) 2^-23 and
  * normals come from Box-Muller on consecutive word pairs.  Results therefore
  * depend only on (seed, substream, global sample index), never on launch
  * shape, batching or sharding.
@@ -107,27 +108,37 @@ int ppabc_device_check(void);
 int ppabc_philox_raw(uint64_t seed, const uint32_t *ctr, uint64_t n,
                      uint32_t *out, void *stream);
 
+/* The two binary32 evaluations of Box-Muller (Sec. 3.4, the transform of the
+ * paper's MKL calls) in the library: polynomial -2 ln u and sin/cos (the
+ * p-value, Algorithm 2 and toggle-switch kernels), and table-driven ones
+ * (Tang's log tables and a two-level sin/cos table in shared memory: the OU
+ * path kernels).  Both are within about 1 ulp of the binary64 transform. */
+#define PPABC_BM_POLY 0u
+#define PPABC_BM_TABLE 1u
+
 /*
- * Standard normals j0 .. j0+n-1 of stream (seed, c1, c2, tag), in binary32:
- * normal j is lane j%4 of counter block (j/4, c1, c2, tag) after Box-Muller
- * (the transform the paper's MKL calls use, Sec. 3.4).  z is [n] float.
+ * Standard normals j0 .. j0+n-1 of stream (seed, index c1, substream c2,
+ * tag), in binary32: normal j is lane j%4 of counter (tag, j/4, c2, c1)
+ * after the Box-Muller evaluation `method` (PPABC_BM_POLY or
+ * PPABC_BM_TABLE; EINVAL otherwise).  z is [n] float.
  */
 int ppabc_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag,
-                  uint64_t j0, uint64_t n, float *z, void *stream);
+                  uint64_t j0, uint64_t n, uint32_t method, float *z, void *stream);
 
 /*
  * Box-Muller transform of given word pairs, in binary32: w is [n][2] uint32
  * (even, odd), z is [n][2] float with z_even = r cos 2 pi u(w_odd),
- * z_odd = r sin 2 pi u(w_odd), r = sqrt(-2 ln u(w_even)).  Exposes the
- * transform every normal of the library goes through, so it can be checked
- * on all 2^23 uniforms.  w and z 8-byte aligned.
+ * z_odd = r sin 2 pi u(w_odd), r = sqrt(-2 ln u(w_even)), by the evaluation
+ * `method` (PPABC_BM_POLY or PPABC_BM_TABLE).  Exposes the transforms every
+ * normal of the library goes through, so each can be checked on all 2^23
+ * uniforms.  w and z 8-byte aligned.
  */
-int ppabc_box_muller(const uint32_t *w, uint64_t n, float *z, void *stream);
+int ppabc_box_muller(const uint32_t *w, uint64_t n, uint32_t method, float *z, void *stream);
 
 /*
  * Prior-predictive sampling for ABC (Sec. 3.1, Eq. 2; Algorithm 1 with N
  * fixed), one sample per global index g = sample_base + i, i < n_samples:
- *   theta ~ prior        (counter (0, g, substream, PRIOR), words 0..2),
+ *   theta ~ prior        (counter (PRIOR, 0, substream, g), words 0..2),
  *   X_s = X_{s-1} + th1 (th2 - X_{s-1}) dt + th3 sqrt(dt) xi_{s-1},
  *                        (xi_j: normal j of stream (seed, g, substream, PATH)),
  *   S(D*) = (X_{s_1}, .., X_{s_nobs}),  rho = || S(D*) - y_obs ||_2.
@@ -288,10 +299,10 @@ typedef struct ppabc_abc_job {
 } ppabc_abc_job;
 
 /*
- * Tile shape of the persistent kernel: `threads` per CTA (128 or 256) and the
+ * Tile shape of the persistent kernel: `threads` per CTA (256 or 512) and the
  * least number of Euler-Maruyama steps one thread runs per tile (a job with S
  * steps gets ceil(min_tile_steps / S) samples per thread, capped at 64).
- * NULL selects (128, 4096).  The Python binding's autotuner picks it.
+ * NULL selects (512, 4096).  The Python binding's autotuner picks it.
  */
 typedef struct ppabc_tile_config {
   uint32_t threads;
@@ -416,7 +427,7 @@ int ppabc_server_destroy(ppabc_server *s);
  * Prior-predictive p-value sweep (Sec. 4.1, Eq. 6 and Eq. 8) for the
  * conjugate model y_i ~ N(mu, 1), i = 1..n_obs, mu ~ N(0, lambda_k^2).  For
  * lambda index k < n_lambda and data set m = set_base .. set_base+m_sets-1,
- * with z_t the normals of stream (seed, m, k, PATH):
+ * with z_t the normals of stream (seed, index m, substream k, PATH):
  *   ybar = lambda_k z_0 + (1/n_obs) sum_{t=1..n_obs} z_t,
  *   counts[k] = #{m : |ybar| >= |ybar_obs|}  (exact, uint64),
  *   p_out[k]  = counts[k] / m_sets.
@@ -460,12 +471,13 @@ typedef struct ppabc_toggle_model {
 
 /*
  * Toggle-switch prior predictive for ABC, one sample per global index
- * g = sample_base + i: theta from blocks (0|1, g, substream, TOGGLE_PRIOR);
+ * g = sample_base + i: theta from counters (TOGGLE_PRIOR, 0|1, substream, g);
  * cell c evolves from u = v = 10 with, at step j = 1..T-1,
  *   u = max(0.97 u + alpha_u / (1 + v^beta_u) - 1 + 0.5 zeta_u, 1),
  *   v = max(0.97 v + alpha_v / (1 + u^beta_v) - 1 + 0.5 zeta_v, 1)
  * (both from the previous u, v; zeta_u, zeta_v are normals 2(j-1), 2(j-1)+1
- * of stream (g, c, (substream << 8) | TOGGLE_PATH)), and is observed as
+ * of stream (index c, substream g, tag (substream << 8) | TOGGLE_PATH)),
+ * and is observed as
  * y = max(u + mu + mu sigma eta / u^gamma, 1), eta = normal 2(T-1).
  * S(D*) = the quantiles at levels k/20, k = 1..19 (linear interpolation
  * between order statistics: h = (C-1) k / 20), rho = ||S - q_obs||_2.
@@ -488,8 +500,8 @@ int toggle_prior_predictive(const ppabc_toggle_model *h_model, const double *h_q
  * Weak-informativity test (Sec. 4.1, Eq. 9 and Algorithm 2) for the
  * conjugate model y_i ~ N(mu, 1), i = 1..n_obs, mu ~ N(0, lambda^2), base
  * hyperparameter lambda0.  For each k < n_lambda:
- *   base sets   i < N: ybar_0^i of stream (seed, i, k, BASE) with lambda0,
- *   lambda sets j < N: ybar_k^j of stream (seed, j, k, PATH) with lambda[k],
+ *   base sets   i < N: ybar_0^i of stream (seed, index i, substream k, BASE), lambda0,
+ *   lambda sets j < N: ybar_k^j of stream (seed, index j, substream k, PATH), lambda[k],
  *   count_k^i = #{j : |ybar_k^j| >= |ybar_0^i|}      (p_k^i = count_k^i / N),
  *   gamma_out[k] = the ceil(alpha N)-th smallest p_k^i (the alpha quantile).
  * Priors with gamma_k > gamma_0 for lambda_0 = lambda0 are weakly informative

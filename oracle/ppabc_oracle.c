@@ -91,10 +91,11 @@ void orc_box_muller_words(const uint32_t *w, uint64_t n, double *z) {
   for (uint64_t i = 0; i < n; ++i) box_muller(w[2 * i], w[2 * i + 1], &z[2 * i], &z[2 * i + 1]);
 }
 
-/* The four normals of counter block (b, c1, c2, tag). */
+/* The four normals of block b of the stream (index c1, substream c2, tag):
+ * counter (tag, b, c2, c1). */
 static void block_normals(const uint32_t key[2], uint32_t b, uint32_t c1,
                           uint32_t c2, uint32_t tag, double z[4]) {
-  uint32_t ctr[4] = {b, c1, c2, tag};
+  uint32_t ctr[4] = {tag, b, c2, c1};
   uint32_t w[4];
   orc_philox4x32_10(ctr, key, w);
   box_muller(w[0], w[1], &z[0], &z[1]);
@@ -121,7 +122,7 @@ void orc_stream_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag,
  *
  * For sample i:
  *   1. theta* ~ pi(theta): th_j = lo_j + (hi_j - lo_j) u(w_j), w = Philox
- *      block (0, i, sub, PRIOR) (uniform priors, as in the paper's sampler).
+ *      counter (PRIOR, 0, sub, i) (uniform priors, as in the paper's sampler).
  *   2. D* ~ s(D; theta*): X_0 = x0 and for s = 1..S
  *        X_s = X_{s-1} + th1 (th2 - X_{s-1}) dt + th3 sqrt(dt) xi_{s-1},
  *      xi_j = normal j of stream (seed, i, sub, PATH).
@@ -132,7 +133,7 @@ void orc_stream_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag,
 static void ou_one_sample(const orc_ou_model *m, const double *y_obs,
                           const uint32_t key[2], uint64_t i, uint32_t sub,
                           double *theta, double *summ, double *dist) {
-  uint32_t prior_ctr[4] = {0u, (uint32_t)i, sub, ORC_TAG_PRIOR};
+  uint32_t prior_ctr[4] = {ORC_TAG_PRIOR, 0u, sub, (uint32_t)i};
   uint32_t w[4];
   orc_philox4x32_10(prior_ctr, key, w);
   double th[3];
@@ -529,8 +530,8 @@ static void toggle_one_sample(const orc_toggle_model *m, const double *q_obs,
                               const uint32_t key[2], uint64_t g, uint32_t sub, double *theta,
                               double *summ, double *ycell, double *uv, double *dist, double *ybuf) {
   uint32_t w0[4], w1[4];
-  uint32_t c0[4] = {0u, (uint32_t)g, sub, ORC_TAG_TOGGLE_PRIOR};
-  uint32_t c1[4] = {1u, (uint32_t)g, sub, ORC_TAG_TOGGLE_PRIOR};
+  uint32_t c0[4] = {ORC_TAG_TOGGLE_PRIOR, 0u, sub, (uint32_t)g};
+  uint32_t c1[4] = {ORC_TAG_TOGGLE_PRIOR, 1u, sub, (uint32_t)g};
   orc_philox4x32_10(c0, key, w0);
   orc_philox4x32_10(c1, key, w1);
   const uint32_t words[7] = {w0[0], w0[1], w0[2], w0[3], w1[0], w1[1], w1[2]};
@@ -550,10 +551,10 @@ static void toggle_one_sample(const orc_toggle_model *m, const double *q_obs,
       double p_u = pow(v, beta_u);
       double p_v = pow(u, beta_v);
       double zu, zv;
-      if (zi % 4 == 0) block_normals(key, zi / 4, (uint32_t)g, c, tag, z);
+      if (zi % 4 == 0) block_normals(key, zi / 4, c, (uint32_t)g, tag, z);
       zu = z[zi % 4];
       ++zi;
-      if (zi % 4 == 0) block_normals(key, zi / 4, (uint32_t)g, c, tag, z);
+      if (zi % 4 == 0) block_normals(key, zi / 4, c, (uint32_t)g, tag, z);
       zv = z[zi % 4];
       ++zi;
       u = 0.97 * u + alpha_u / (1.0 + p_u) - 1.0 + 0.5 * zu;
@@ -565,7 +566,7 @@ static void toggle_one_sample(const orc_toggle_model *m, const double *q_obs,
       uv[2 * c] = u;
       uv[2 * c + 1] = v;
     }
-    if (zi % 4 == 0) block_normals(key, zi / 4, (uint32_t)g, c, tag, z);
+    if (zi % 4 == 0) block_normals(key, zi / 4, c, (uint32_t)g, tag, z);
     double eta = z[zi % 4];
     double yv = u + mu + mu * sigma * eta / pow(u, gam);
     if (yv < 1.0) yv = 1.0;

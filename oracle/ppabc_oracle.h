@@ -12,7 +12,9 @@
  * Conventions shared *by definition* (not by code) with the CUDA path:
  *   - Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) keyed by the 64-bit
  *     seed split as key = (seed & 0xffffffff, seed >> 32);
- *   - counter = (c0 block, c1 sample or data-set index, c2 substream, c3 tag);
+ *   - counter = (c0 tag, c1 block, c2 substream, c3 sample or data-set index):
+ *     normal j of the stream (index, substream, tag) is lane j%4 of the
+ *     block j/4, and a prior draw is block 0 of its tag;
  *   - uniform  u(w) = ((w >> 9) + 1/2) * 2^-23, an exact value in (0,1);
  *   - Box-Muller: (w_even, w_odd) -> r = sqrt(-2 ln u(w_even)),
  *     z_even = r cos(2 pi u(w_odd)), z_odd = r sin(2 pi u(w_odd)).
@@ -59,13 +61,13 @@ double orc_u01(uint32_t w);
 /* Box-Muller on given word pairs: w is [n][2] (even, odd), z is [n][2]. */
 void orc_box_muller_words(const uint32_t *w, uint64_t n, double *z);
 
-/* Normals j0 .. j0+n-1 of stream (seed, c1, c2, tag): normal j comes from
- * counter block j/4, lane j%4. */
+/* Normals j0 .. j0+n-1 of stream (seed, index c1, substream c2, tag): normal
+ * j comes from counter (tag, j/4, c2, c1), lane j%4. */
 void orc_stream_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag,
                         uint64_t j0, uint64_t n, double *z);
 
-/* Prior-predictive OU samples i = base .. base+n-1 (sample index enters the
- * counter as c1).  Outputs (each may be NULL except dist):
+/* Prior-predictive OU samples i = base .. base+n-1 (the sample index is the
+ * stream index, counter word c3).  Outputs (each may be NULL except dist):
  *   theta [n][3], summ [n][n_obs] (X at the observation steps), dist [n].
  * Returns 0, or -1 on invalid arguments. */
 int orc_ou_prior_predictive(const orc_ou_model *m, const double *y_obs,
@@ -89,7 +91,7 @@ void orc_moments(const double *theta, const uint64_t *idx, uint64_t k,
 
 /* Prior-predictive p-value sweep for y_i ~ N(mu,1), i=1..n, mu ~ N(0,lam^2):
  * for each lambda_k and data set m = base..base+M-1 the normals of stream
- * (seed, c1 = m, c2 = k, PATH) give mu = lam_k z_0 and
+ * (seed, index m, substream k, PATH) give mu = lam_k z_0 and
  * ybar = mu + (1/n) sum_{i=1..n} z_i; counts[k] = #{m : |ybar| >= |ybar_obs|},
  * p[k] = counts[k] / M.  ybar (nullable) is [n_lambda][M]. */
 int orc_pvalue_sweep(const double *lambda, uint32_t n_lambda, uint32_t n_obs,
@@ -98,8 +100,8 @@ int orc_pvalue_sweep(const double *lambda, uint32_t n_lambda, uint32_t n_obs,
 
 /* Weak-informativity test (Algorithm 2) for the conjugate normal model, with
  * the sufficient statistic ybar.  For each k < n_lambda:
- *   base sets   i < N: ybar0 from stream (seed, i, k, BASE) with lambda_0,
- *   lambda sets j < N: ybar  from stream (seed, j, k, PATH) with lambda_k,
+ *   base sets   i < N: ybar0 from stream (seed, index i, substream k, BASE), lambda_0,
+ *   lambda sets j < N: ybar  from stream (seed, index j, substream k, PATH), lambda_k,
  *   p_k^i = #{j : |ybar_k^j| >= |ybar0_k^i|} / N           (indicator estimate)
  *   gamma_k = the ceil(alpha N)-th smallest of p_k^1..p_k^N (alpha quantile).
  * counts (nullable) is [n_lambda][N] (the numerators of p_k^i). */
@@ -113,10 +115,11 @@ int orc_weakinf(const double *lambda, uint32_t n_lambda, double lambda0, uint32_
  * u = v = 10, then observed with noise; summaries are the 19 quantiles at
  * levels 0.05 .. 0.95 (linear interpolation between order statistics).
  * Random numbers, for sample g:
- *   prior:  blocks (0, g, sub, TOGGLE_PRIOR) words 0..3 -> theta_0..3 and
- *           (1, g, sub, TOGGLE_PRIOR) words 0..2 -> theta_4..6;
- *   cell c: stream (g, c, (sub << 8) | TOGGLE_PATH): normal 2(j-1) and
- *           2(j-1)+1 drive u and v at step j = 1..T-1, normal 2(T-1) is eta. */
+ *   prior:  counters (TOGGLE_PRIOR, 0, sub, g) words 0..3 -> theta_0..3 and
+ *           (TOGGLE_PRIOR, 1, sub, g) words 0..2 -> theta_4..6;
+ *   cell c: stream (index c, substream g, tag (sub << 8) | TOGGLE_PATH):
+ *           normal 2(j-1) and 2(j-1)+1 drive u and v at step j = 1..T-1,
+ *           normal 2(T-1) is eta. */
 typedef struct orc_toggle_model {
   double lo[7];
   double hi[7];

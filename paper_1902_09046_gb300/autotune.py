@@ -19,7 +19,7 @@ import torch
 
 from . import binding
 
-CANDIDATES = ((128, 1024), (128, 4096), (128, 16384))
+CANDIDATES = ((512, 1024), (512, 4096), (512, 16384), (256, 4096))
 
 
 def _cache_path() -> str:

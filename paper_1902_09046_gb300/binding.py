@@ -158,8 +158,8 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
             "ppabc_last_error": ([], ctypes.c_char_p),
             "ppabc_device_check": ([], i32),
             "ppabc_philox_raw": ([u64, P, u64, P, P], i32),
-            "ppabc_normals": ([u64, u32, u32, u32, u64, u64, P, P], i32),
-            "ppabc_box_muller": ([P, u64, P, P], i32),
+            "ppabc_normals": ([u64, u32, u32, u32, u64, u64, u32, P, P], i32),
+            "ppabc_box_muller": ([P, u64, u32, P, P], i32),
             "abc_prior_predictive": ([M, P, u64, u64, u64, u32, P, P, P, P], i32),
             "abc_select_workspace_bytes": ([u64], sz),
             "abc_select": ([P, u64, u64, dbl, M, u64, u64, u32, P, P, P, u64, P, P, P, P, sz, P], i32),
@@ -233,18 +233,26 @@ def philox_raw(seed: int, ctr: torch.Tensor, stream=None) -> torch.Tensor:
     return out
 
 
-def normals(seed: int, c1: int, c2: int, tag: int, j0: int, n: int, stream=None) -> torch.Tensor:
+BM_POLY = 0
+BM_TABLE = 1
+
+
+def normals(seed: int, c1: int, c2: int, tag: int, j0: int, n: int, method: int = BM_TABLE,
+            stream=None) -> torch.Tensor:
+    """Normals j0..j0+n-1 of stream (index c1, substream c2, tag) by the
+    Box-Muller evaluation `method` (BM_TABLE: the OU path kernels', BM_POLY:
+    the p-value, Algorithm 2 and toggle kernels')."""
     z = torch.empty(n, dtype=torch.float32, device="cuda")
-    _check(load_library().ppabc_normals(seed, c1, c2, tag, j0, n, _ptr(z), _stream(stream)))
+    _check(load_library().ppabc_normals(seed, c1, c2, tag, j0, n, method, _ptr(z), _stream(stream)))
     return z
 
 
-def box_muller(w: torch.Tensor, stream=None) -> torch.Tensor:
+def box_muller(w: torch.Tensor, method: int = BM_TABLE, stream=None) -> torch.Tensor:
     """w: [n,2] uint32 (CUDA) -> [n,2] float32 Box-Muller normals."""
     if w.dtype != torch.uint32 or w.dim() != 2 or w.shape[1] != 2:
         raise ValueError("w must be a [n,2] uint32 tensor")
     z = torch.empty(w.shape, dtype=torch.float32, device=w.device)
-    _check(load_library().ppabc_box_muller(_ptr(w), w.shape[0], _ptr(z), _stream(stream)))
+    _check(load_library().ppabc_box_muller(_ptr(w), w.shape[0], method, _ptr(z), _stream(stream)))
     return z
 
 
@@ -516,7 +524,7 @@ class Batch:
         self.n = n
         ws_bytes = int(self.lib.ppabc_batch_workspace_bytes(self.arr, n))
         self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
-        self.cfg = TileConfig(*(tile or (128, 4096)))
+        self.cfg = TileConfig(*(tile or (512, 4096)))
         self.plan = ctypes.c_void_p()
         _check(self.lib.ppabc_batch_prepare(self.arr, n, ctypes.byref(self.cfg), _ptr(self.ws),
                                             ws_bytes, _stream(stream), ctypes.byref(self.plan)))

@@ -39,13 +39,28 @@ struct BatchJobDev {
 
 inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
+// The Box-Muller tables sit in shared memory: 512-thread CTAs hold the
+// lane-replicated log table (80 KB, two CTAs per SM), 256-thread CTAs the
+// compact one (50 KB, four per SM); the values, and so the results, are the
+// same.
 template <int kThreads>
-__global__ void __launch_bounds__(kThreads, 1152 / kThreads) em_ou_batch(const BatchJobDev* __restrict__ jobs,
+constexpr bool batch_rep_log() { return kThreads >= 512; }
+
+template <int kThreads>
+constexpr size_t batch_smem() { return bm_smem_bytes<batch_rep_log<kThreads>()>(); }
+
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads, 1024 / kThreads) em_ou_batch(const BatchJobDev* __restrict__ jobs,
                                                         const uint32_t* __restrict__ order,
                                                         uint32_t n_jobs, unsigned int* head,
                                                         unsigned int* cursors) {
+  constexpr bool kRep = batch_rep_log<kThreads>();
+  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_job;
   __shared__ uint32_t s_tile;
+  bm_load<kRep>(smem);
+  __syncthreads();
+  const BmTab T = bm_tab<kRep>(smem);
   for (;;) {
     if (threadIdx.x == 0) {
       int jj = -1;
@@ -85,7 +100,7 @@ __global__ void __launch_bounds__(kThreads, 1152 / kThreads) em_ou_batch(const B
         ou_prior(J.P, gi[0], th1[0], th2[0], th3[0]);
         ou_prior(J.P, gi[1], th1[1], th2[1], th3[1]);
         double d[2];
-        ou_path2<false>(J.P, gi, th1, th2, th3, nullptr, nullptr, 0, d);
+        ou_path2<false, kRep>(J.P, T, gi, th1, th2, th3, nullptr, nullptr, 0, d);
         J.dist[i0] = d[0];
         if (i1 < n) J.dist[i1] = d[1];
       }
@@ -95,7 +110,7 @@ __global__ void __launch_bounds__(kThreads, 1152 / kThreads) em_ou_batch(const B
       if (i < n) {
         float th1, th2, th3;
         ou_prior(J.P, i, th1, th2, th3);
-        J.dist[i] = ou_path<false>(J.P, i, th1, th2, th3, nullptr, 0);
+        J.dist[i] = ou_path<false, kRep>(J.P, T, i, th1, th2, th3, nullptr, 0);
       }
     }
   }
@@ -123,7 +138,7 @@ using namespace ppabc;
 // Host-side plan of a prepared batch (opaque to callers).
 struct ppabc_batch_plan {
   uint32_t n_jobs = 0;
-  uint32_t threads = 128;
+  uint32_t threads = 512;
   int grid = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -206,10 +221,10 @@ int ppabc_batch_prepare(const ppabc_abc_job* h_jobs, uint32_t n_jobs,
   *plan_out = nullptr;
   int rc = validate_jobs(h_jobs, n_jobs);
   if (rc) return rc;
-  const uint32_t threads = h_cfg ? h_cfg->threads : 128u;
+  const uint32_t threads = h_cfg ? h_cfg->threads : 512u;
   const uint32_t min_steps = h_cfg ? h_cfg->min_tile_steps : 4096u;
-  if (threads != 128u && threads != 256u)
-    return set_error(PPABC_EINVAL, "tile threads must be 128 or 256");
+  if (threads != 256u && threads != 512u)
+    return set_error(PPABC_EINVAL, "tile threads must be 256 or 512");
   if (min_steps == 0) return set_error(PPABC_EINVAL, "min_tile_steps must be >= 1");
   const Layout L = layout_of(h_jobs, n_jobs);
   if (!workspace || workspace_bytes < L.total)
@@ -275,10 +290,17 @@ int ppabc_batch_prepare(const ppabc_abc_job* h_jobs, uint32_t n_jobs,
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (threads == 128)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, em_ou_batch<128>, 128, 0);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, em_ou_batch<256>, 256, 0);
+  e = cudaFuncSetAttribute(em_ou_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(batch_smem<256>()));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(em_ou_batch<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(batch_smem<512>()));
+  if (e == cudaSuccess) {
+    if (threads == 256)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, em_ou_batch<256>, 256, batch_smem<256>());
+    else
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, em_ou_batch<512>, 512, batch_smem<512>());
+  }
   if (e != cudaSuccess) {
     delete plan;
     return check_cuda(e, "occupancy query");
@@ -302,10 +324,12 @@ int ppabc_batch_launch(ppabc_batch_plan* plan, void* stream) {
   if (e != cudaSuccess) return check_cuda(e, "batch scheduler reset");
   unsigned int* head = plan->d_sched;
   unsigned int* cursors = plan->d_sched + 1;
-  if (plan->threads == 128)
-    em_ou_batch<128><<<plan->grid, 128, 0, s>>>(plan->d_jobs, plan->d_order, n_jobs, head, cursors);
+  if (plan->threads == 256)
+    em_ou_batch<256><<<plan->grid, 256, batch_smem<256>(), s>>>(plan->d_jobs, plan->d_order, n_jobs, head,
+                                                                cursors);
   else
-    em_ou_batch<256><<<plan->grid, 256, 0, s>>>(plan->d_jobs, plan->d_order, n_jobs, head, cursors);
+    em_ou_batch<512><<<plan->grid, 512, batch_smem<512>(), s>>>(plan->d_jobs, plan->d_order, n_jobs, head,
+                                                                cursors);
   e = cudaGetLastError();
   if (e != cudaSuccess) return check_cuda(e, "em_ou_batch launch");
   for (uint32_t j = 0; j < n_jobs; ++j) {

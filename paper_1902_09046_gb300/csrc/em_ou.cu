@@ -6,18 +6,27 @@
 // This replaces the paper's block-of-VECL SIMD loop with pre-generated
 // normals (Sec. 3.4): on the GPU a warp is the SIMD vector, the sample index
 // is the lane, and the normals never touch memory.
+#include <atomic>
+
 #include "internal.h"
 
 namespace ppabc {
 
-constexpr int kEmThreads = 128;
+// The path kernels keep the Box-Muller tables in shared memory (80 KB with
+// the lane-replicated log table): 512-thread CTAs, two per SM, 32 warps.
+constexpr int kEmThreads = 512;
+constexpr size_t kEmSmem = bm_smem_bytes<true>();
 
 template <bool kWantTheta, bool kWantSumm>
-__global__ void __launch_bounds__(kEmThreads) em_ou_fused(const __grid_constant__ OUConst P,
-                                                          uint32_t base, uint32_t n,
-                                                          float* __restrict__ theta_out,
-                                                          double* __restrict__ summ_out,
-                                                          double* __restrict__ dist_out) {
+__global__ void __launch_bounds__(kEmThreads, 2) em_ou_fused(const __grid_constant__ OUConst P,
+                                                             uint32_t base, uint32_t n,
+                                                             float* __restrict__ theta_out,
+                                                             double* __restrict__ summ_out,
+                                                             double* __restrict__ dist_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  bm_load<true>(smem);
+  __syncthreads();
+  const BmTab T = bm_tab<true>(smem);
   const uint32_t i = blockIdx.x * kEmThreads + threadIdx.x;
   if (i >= n) return;
   const uint32_t g = base + i;
@@ -28,15 +37,19 @@ __global__ void __launch_bounds__(kEmThreads) em_ou_fused(const __grid_constant_
     theta_out[static_cast<size_t>(n) + i] = th2;
     theta_out[2 * static_cast<size_t>(n) + i] = th3;
   }
-  dist_out[i] = ou_path<kWantSumm>(P, g, th1, th2, th3, kWantSumm ? summ_out + i : nullptr, n);
+  dist_out[i] = ou_path<kWantSumm, true>(P, T, g, th1, th2, th3, kWantSumm ? summ_out + i : nullptr, n);
 }
 
-// Two samples per thread (samples i and i + half of each CTA's 2x128
-// range), interleaved; see ou_path2.  Used when neither theta nor the
-// summaries are requested (the benchmark and batch paths).
-__global__ void __launch_bounds__(kEmThreads, 10) em_ou_fused_x2(const __grid_constant__ OUConst P,
-                                                             uint32_t base, uint32_t n,
-                                                             double* __restrict__ dist_out) {
+// Two samples per thread (samples i and i + kEmThreads of each CTA's
+// 2 kEmThreads range), interleaved; see ou_path2.  Used when neither theta
+// nor the summaries are requested (the benchmark and batch paths).
+__global__ void __launch_bounds__(kEmThreads, 2) em_ou_fused_x2(const __grid_constant__ OUConst P,
+                                                                uint32_t base, uint32_t n,
+                                                                double* __restrict__ dist_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  bm_load<true>(smem);
+  __syncthreads();
+  const BmTab T = bm_tab<true>(smem);
   const uint32_t i0 = blockIdx.x * (2 * kEmThreads) + threadIdx.x;
   const uint32_t i1 = i0 + kEmThreads;
   if (i0 >= n) return;
@@ -45,7 +58,7 @@ __global__ void __launch_bounds__(kEmThreads, 10) em_ou_fused_x2(const __grid_co
   ou_prior(P, gi[0], th1[0], th2[0], th3[0]);
   ou_prior(P, gi[1], th1[1], th2[1], th3[1]);
   double d[2];
-  ou_path2<false>(P, gi, th1, th2, th3, nullptr, nullptr, 0, d);
+  ou_path2<false, true>(P, T, gi, th1, th2, th3, nullptr, nullptr, 0, d);
   dist_out[i0] = d[0];
   if (i1 < n) dist_out[i1] = d[1];
 }
@@ -58,14 +71,22 @@ __global__ void __launch_bounds__(kEmThreads, 10) em_ou_fused_x2(const __grid_co
 // blocks per round, while warp 0 runs the samples' Euler-Maruyama paths
 // (lane = sample) over the previous round's blocks.  The path arithmetic is
 // ou_path's, block by block in the same order, so the distances are bit for
-// bit those of the other kernels.  Rounds end at a CTA barrier; nothing spins.
+// bit those of the other kernels (the compact copy of the log table holds the
+// same values as the replicated one).  Rounds end at a CTA barrier; nothing
+// spins.
 constexpr int kPipeProducers = 6;
 constexpr int kPipeRound = 12;
 constexpr int kPipeThreads = 32 * (1 + kPipeProducers);
+constexpr size_t kPipeRingBytes = 2 * kPipeRound * 32 * sizeof(float4);
+constexpr size_t kPipeSmem = kPipeRingBytes + bm_smem_bytes<false>();
 
 __global__ void __launch_bounds__(kPipeThreads) em_ou_pipe(const __grid_constant__ OUConst P, uint32_t base,
                                                            uint32_t n, double* __restrict__ dist_out) {
-  __shared__ float4 ring[2][kPipeRound][32];
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4 (*ring)[kPipeRound][32] = reinterpret_cast<float4 (*)[kPipeRound][32]>(smem);
+  unsigned char* tabs = smem + kPipeRingBytes;
+  bm_load<false>(tabs);
+  __syncthreads();
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t i = blockIdx.x * 32 + lane;
   const bool valid = i < n;
@@ -77,12 +98,15 @@ __global__ void __launch_bounds__(kPipeThreads) em_ou_pipe(const __grid_constant
   const uint32_t n_blocks = (P.s_obs[n_obs - 1] + 3u) >> 2;  // blocks up to the last observation
   const uint32_t rounds = (n_blocks + kPipeRound - 1) / kPipeRound;
   if (warp > 0) {
-    const PhiloxStream stream = philox_stream(P.keys, g, P.sub, kTagPath);
+    const BmTab T = bm_tab<false>(tabs);
+    const PhiloxFamily fam = philox_family(P.keys, kTagPath, P.sub);
+    const PhiloxStream stream = philox_stream(P.keys, fam, g);
     for (uint32_t r = 0; r <= rounds; ++r) {
       if (r < rounds) {
         for (uint32_t q = warp - 1; q < static_cast<uint32_t>(kPipeRound); q += kPipeProducers) {
           const uint32_t b = r * kPipeRound + q;
-          if (b < n_blocks) ring[r & 1u][q][lane] = scaled_normals_of(philox_block(stream, P.keys, b), c);
+          if (b < n_blocks)
+            ring[r & 1u][q][lane] = scaled_tnormals_of<false>(T, philox_block(P.keys, fam, stream, b), c);
         }
       }
       __syncthreads();
@@ -145,28 +169,52 @@ __global__ void __launch_bounds__(kPipeThreads) em_ou_pipe(const __grid_constant
 
 constexpr uint32_t kPipeMaxN = 49152;  // above about this the two-path kernel is faster
 
+cudaError_t bm_hooks_prepare();
+
+cudaError_t em_prepare() {
+  static std::atomic<unsigned long long> ready{0ull};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (ready.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  const int big = static_cast<int>(kEmSmem);
+  e = cudaFuncSetAttribute(em_ou_fused_x2, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(em_ou_fused<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(em_ou_fused<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(em_ou_fused<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(em_ou_fused<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(em_ou_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kPipeSmem));
+  if (e == cudaSuccess) e = bm_hooks_prepare();
+  if (e == cudaSuccess && bit) ready.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
 cudaError_t launch_em_ou(const OUConst& P, uint64_t base, uint32_t n, float* theta_out,
                          double* summ_out, double* dist_out, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
+  cudaError_t e = em_prepare();
+  if (e != cudaSuccess) return e;
   if (!theta_out && !summ_out && n <= kPipeMaxN) {
-    em_ou_pipe<<<(n + 31) / 32, kPipeThreads, 0, s>>>(P, static_cast<uint32_t>(base), n, dist_out);
+    em_ou_pipe<<<(n + 31) / 32, kPipeThreads, kPipeSmem, s>>>(P, static_cast<uint32_t>(base), n, dist_out);
     return cudaGetLastError();
   }
   if (!theta_out && !summ_out) {
     const dim3 grid2((n + 2 * kEmThreads - 1) / (2 * kEmThreads));
-    em_ou_fused_x2<<<grid2, kEmThreads, 0, s>>>(P, static_cast<uint32_t>(base), n, dist_out);
+    em_ou_fused_x2<<<grid2, kEmThreads, kEmSmem, s>>>(P, static_cast<uint32_t>(base), n, dist_out);
     return cudaGetLastError();
   }
   const dim3 grid((n + kEmThreads - 1) / kEmThreads);
   const uint32_t b = static_cast<uint32_t>(base);
   if (theta_out && summ_out)
-    em_ou_fused<true, true><<<grid, kEmThreads, 0, s>>>(P, b, n, theta_out, summ_out, dist_out);
+    em_ou_fused<true, true><<<grid, kEmThreads, kEmSmem, s>>>(P, b, n, theta_out, summ_out, dist_out);
   else if (theta_out)
-    em_ou_fused<true, false><<<grid, kEmThreads, 0, s>>>(P, b, n, theta_out, summ_out, dist_out);
+    em_ou_fused<true, false><<<grid, kEmThreads, kEmSmem, s>>>(P, b, n, theta_out, summ_out, dist_out);
   else if (summ_out)
-    em_ou_fused<false, true><<<grid, kEmThreads, 0, s>>>(P, b, n, theta_out, summ_out, dist_out);
+    em_ou_fused<false, true><<<grid, kEmThreads, kEmSmem, s>>>(P, b, n, theta_out, summ_out, dist_out);
   else
-    em_ou_fused<false, false><<<grid, kEmThreads, 0, s>>>(P, b, n, theta_out, summ_out, dist_out);
+    em_ou_fused<false, false><<<grid, kEmThreads, kEmSmem, s>>>(P, b, n, theta_out, summ_out, dist_out);
   return cudaGetLastError();
 }
 
@@ -179,31 +227,68 @@ __global__ void philox_raw_kernel(const __grid_constant__ PhiloxKeys K, const ui
   if (i < n) out[i] = philox4x32_10(ctr[i], K);
 }
 
+// method 0 (PPABC_BM_POLY): the polynomial transform of rng.cuh, used by the
+// p-value, Algorithm 2 and toggle kernels; method 1 (PPABC_BM_TABLE): the
+// table-driven transform of bm_table.cuh, used by the OU path kernels.
+constexpr size_t kHookSmem = bm_smem_bytes<false>();
+
+template <int kMethod>
 __global__ void normals_kernel(const __grid_constant__ PhiloxKeys K, uint32_t c1, uint32_t c2,
                                uint32_t tag, uint64_t j0, uint64_t n, float* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (kMethod == 1) {
+    bm_load<false>(smem);
+    __syncthreads();
+  }
   const uint64_t t = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const uint64_t j = j0 + t;
-  const PhiloxStream S = philox_stream(K, c1, c2, tag);
-  const float4 q = normals_of(philox_block(S, K, static_cast<uint32_t>(j >> 2)));
+  const PhiloxFamily F = philox_family(K, tag, c2);
+  const PhiloxStream S = philox_stream(K, F, c1);
+  const uint4 w = philox_block(K, F, S, static_cast<uint32_t>(j >> 2));
+  const float4 q = kMethod == 1 ? tnormals_of<false>(bm_tab<false>(smem), w) : normals_of(w);
   const uint32_t lane = static_cast<uint32_t>(j & 3u);
   z[t] = lane == 0 ? q.x : lane == 1 ? q.y : lane == 2 ? q.z : q.w;
 }
 
+template <int kMethod>
 __global__ void box_muller_kernel(const uint2* __restrict__ w, uint64_t n, float2* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (kMethod == 1) {
+    bm_load<false>(smem);
+    __syncthreads();
+  }
   const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint2 p = w[i];
   float2 q;
-  box_muller(p.x, p.y, q.x, q.y);
+  if (kMethod == 1)
+    box_muller_tab<false>(bm_tab<false>(smem), p.x, p.y, q.x, q.y);
+  else
+    box_muller(p.x, p.y, q.x, q.y);
   z[i] = q;
 }
 
-cudaError_t launch_box_muller(const uint32_t* w, uint64_t n, float* z, cudaStream_t s) {
+cudaError_t bm_hooks_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(normals_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kHookSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(box_muller_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kHookSmem));
+  return e;
+}
+
+cudaError_t launch_box_muller(const uint32_t* w, uint64_t n, uint32_t method, float* z, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
-  box_muller_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const uint2*>(w), n,
-                                           reinterpret_cast<float2*>(z));
+  cudaError_t e = em_prepare();
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = static_cast<unsigned>((n + 1023) / 1024);
+  const uint2* w2 = reinterpret_cast<const uint2*>(w);
+  float2* z2 = reinterpret_cast<float2*>(z);
+  if (method == 1)
+    box_muller_kernel<1><<<blocks, 1024, kHookSmem, s>>>(w2, n, z2);
+  else
+    box_muller_kernel<0><<<blocks, 1024, 0, s>>>(w2, n, z2);
   return cudaGetLastError();
 }
 
@@ -217,10 +302,15 @@ cudaError_t launch_philox_raw(uint64_t seed, const uint32_t* ctr, uint64_t n, ui
 }
 
 cudaError_t launch_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag, uint64_t j0,
-                           uint64_t n, float* z, cudaStream_t s) {
+                           uint64_t n, uint32_t method, float* z, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
-  normals_kernel<<<blocks, 256, 0, s>>>(philox_keys(seed), c1, c2, tag, j0, n, z);
+  cudaError_t e = em_prepare();
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = static_cast<unsigned>((n + 1023) / 1024);
+  if (method == 1)
+    normals_kernel<1><<<blocks, 1024, kHookSmem, s>>>(philox_keys(seed), c1, c2, tag, j0, n, z);
+  else
+    normals_kernel<0><<<blocks, 1024, 0, s>>>(philox_keys(seed), c1, c2, tag, j0, n, z);
   return cudaGetLastError();
 }
 

@@ -25,8 +25,12 @@ int make_ou_const(const ppabc_ou_model* m, const double* h_y_obs, uint64_t seed,
 cudaError_t launch_philox_raw(uint64_t seed, const uint32_t* ctr, uint64_t n, uint32_t* out,
                               cudaStream_t s);
 cudaError_t launch_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag, uint64_t j0,
-                           uint64_t n, float* z, cudaStream_t s);
-cudaError_t launch_box_muller(const uint32_t* w, uint64_t n, float* z, cudaStream_t s);
+                           uint64_t n, uint32_t method, float* z, cudaStream_t s);
+cudaError_t launch_box_muller(const uint32_t* w, uint64_t n, uint32_t method, float* z, cudaStream_t s);
+// Raises the shared-memory limit of the path kernels and the table-driven
+// RNG hooks on the current device (once; launch_em_ou calls it too).  Call
+// before capturing launches.
+cudaError_t em_prepare();
 cudaError_t launch_em_ou(const OUConst& P, uint64_t base, uint32_t n, float* theta_out,
                          double* summ_out, double* dist_out, cudaStream_t s);
 

@@ -1,10 +1,10 @@
 // ou_path.cuh -- one OU prior-predictive sample per thread, fused end to end.
 //
 // For global sample index g (Sec. 3.1, Eq. 2 and Algorithm 1 with N fixed):
-//   theta ~ U(lo, hi)        counter (0, g, sub, PRIOR), words 0..2;
+//   theta ~ U(lo, hi)        counter (PRIOR, 0, sub, g), words 0..2;
 //   X_s = X_{s-1} + th1 dt (th2 - X_{s-1}) + th3 sqrt(dt) xi_{s-1}
 //                            Euler-Maruyama (Eq. 5) on the OU SDE, with xi_j
-//                            lane j%4 of counter block (j/4, g, sub, PATH);
+//                            lane j%4 of counter (PATH, j/4, sub, g);
 //   acc += (X_{s_j} - y_j)^2 at the observation steps s_j;  rho = sqrt(acc).
 //
 // Precision: the state is binary32 with Kahan compensation (X - comp is the
@@ -14,12 +14,14 @@
 // 1e-6 relative band the accept sets are compared in.
 //
 // Nothing is read from or written to global memory inside the step loop: the
-// Philox words, the normals and the state live in registers.
+// Philox words, the normals and the state live in registers, and the
+// Box-Muller tables (bm_table.cuh) in shared memory.
 #pragma once
 
 #include <stdint.h>
 
 #include "../../include/ppabc.h"
+#include "bm_table.cuh"
 #include "rng.cuh"
 
 namespace ppabc {
@@ -43,7 +45,7 @@ struct OUConst {
 // Prior draw of sample g: th_j = lo_j + span_j u(w_j).
 __device__ __forceinline__ void ou_prior(const OUConst& P, uint32_t g, float& th1, float& th2,
                                          float& th3) {
-  const uint4 w = philox4x32_10(make_uint4(0u, g, P.sub, kTagPrior), P.keys);
+  const uint4 w = philox4x32_10(make_uint4(kTagPrior, 0u, P.sub, g), P.keys);
   th1 = fmaf(P.span[0], u01f(w.x), P.lo[0]);
   th2 = fmaf(P.span[1], u01f(w.y), P.lo[1]);
   th3 = fmaf(P.span[2], u01f(w.z), P.lo[2]);
@@ -88,23 +90,6 @@ __device__ __forceinline__ void em_block4(float& Y, float& comp, const Em4& E, f
   Y = t;
 }
 
-// The four normals of counter block b for two samples at once, packed across
-// the samples (lane q = sample q): z[l] holds normal l of each, scaled by
-// c = (th3 sqrt(dt)) of each.  Bit for bit the values scaled_normals_of gives
-// each sample; the normals arrive paired for the packed EM update.
-__device__ __forceinline__ void scaled_normals_x2(uint4 w0, uint4 w1, float2 c, float2 z[4]) {
-  const float2 rA = mul2(c, sqrt_pos2(neg2_log_u01_2(w0.x, w1.x)));
-  float2 sA, cA;
-  sincos_2pi_u01_2(w0.y, w1.y, sA, cA);
-  const float2 rB = mul2(c, sqrt_pos2(neg2_log_u01_2(w0.z, w1.z)));
-  float2 sB, cB;
-  sincos_2pi_u01_2(w0.w, w1.w, sB, cB);
-  z[0] = mul2(rA, cA);
-  z[1] = mul2(rA, sA);
-  z[2] = mul2(rB, cB);
-  z[3] = mul2(rB, sB);
-}
-
 // em_block4 on two samples at once (lane q is sample q), with the same
 // operations in the same order: each lane is bit for bit em_block4's result.
 // x - y is formed as fma(y, -1, x), which rounds identically.
@@ -120,8 +105,8 @@ __device__ __forceinline__ void em_block4_2(float2& Y, float2& comp, float2 a, f
 // when summ is non-null.  X_s = th2 + Y_s with Y_0 = x0 - th2 split exactly
 // into (Y, -comp); observation steps are handled between runs of whole
 // 4-step counter blocks, which take no per-step test.
-template <bool kWantSumm>
-__device__ __forceinline__ double ou_path(const OUConst& P, uint32_t g, float th1, float th2,
+template <bool kWantSumm, bool kRepLog>
+__device__ __forceinline__ double ou_path(const OUConst& P, const BmTab& T, uint32_t g, float th1, float th2,
                                           float th3, double* summ, uint32_t summ_stride) {
   const float k = th1 * P.dt;
   const float c = th3 * P.sqrt_dt;
@@ -138,7 +123,8 @@ __device__ __forceinline__ double ou_path(const OUConst& P, uint32_t g, float th
   const double th2d = static_cast<double>(th2);
   double acc = 0.0;
   const Em4 E4 = em4_constants(k);
-  const PhiloxStream stream = philox_stream(P.keys, g, P.sub, kTagPath);
+  const PhiloxFamily fam = philox_family(P.keys, kTagPath, P.sub);
+  const PhiloxStream stream = philox_stream(P.keys, fam, g);
   uint32_t s = 0;  // steps taken (4 b except inside the last block)
   uint32_t b = 0;  // next counter block
   uint32_t j = 0;  // next observation
@@ -149,9 +135,10 @@ __device__ __forceinline__ double ou_path(const OUConst& P, uint32_t g, float th
     const uint32_t b_end = b + (s_next > s + 4u ? (s_next - s - 1u) >> 2 : 0u);
     s += (b_end - b) << 2;
 #pragma unroll 2
-    for (; b < b_end; ++b) em_block4(Y, comp, E4, scaled_normals_of(philox_block(stream, P.keys, b), c));
+    for (; b < b_end; ++b)
+      em_block4(Y, comp, E4, scaled_tnormals_of<kRepLog>(T, philox_block(P.keys, fam, stream, b), c));
     // The block holding step s_next (and possibly later observation steps).
-    const float4 z = scaled_normals_of(philox_block(stream, P.keys, b), c);
+    const float4 z = scaled_tnormals_of<kRepLog>(T, philox_block(P.keys, fam, stream, b), c);
     ++b;
     const float zz[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
@@ -179,12 +166,13 @@ __device__ __forceinline__ double ou_path(const OUConst& P, uint32_t g, float th
 // chain's Philox wide multiplies occupy the integer multiplier.  Both samples
 // share the launch's step count and observation steps, so the control flow
 // is the same as for one sample.
-template <bool kWantSumm>
-__device__ __forceinline__ void ou_path2(const OUConst& P, const uint32_t g[2], const float th1[2],
+template <bool kWantSumm, bool kRepLog>
+__device__ __forceinline__ void ou_path2(const OUConst& P, const BmTab& T, const uint32_t g[2], const float th1[2],
                                          const float th2[2], const float th3[2], double* summ0,
                                          double* summ1, uint32_t summ_stride, double out[2]) {
   float k[2], Y0[2], comp0[2];
   double th2d[2], acc[2];
+  const PhiloxFamily fam = philox_family(P.keys, kTagPath, P.sub);
   PhiloxStream stream[2];
   Em4 E4[2];
 #pragma unroll
@@ -196,7 +184,7 @@ __device__ __forceinline__ void ou_path2(const OUConst& P, const uint32_t g[2], 
     comp0[q] = -err;
     th2d[q] = static_cast<double>(th2[q]);
     acc[q] = 0.0;
-    stream[q] = philox_stream(P.keys, g[q], P.sub, kTagPath);
+    stream[q] = philox_stream(P.keys, fam, g[q]);
     E4[q] = em4_constants(k[q]);
   }
   const float2 c = make_float2(th3[0] * P.sqrt_dt, th3[1] * P.sqrt_dt);
@@ -212,11 +200,13 @@ __device__ __forceinline__ void ou_path2(const OUConst& P, const uint32_t g[2], 
     s += (b_end - b) << 2;
     for (; b < b_end; ++b) {
       float2 z[4];
-      scaled_normals_x2(philox_block(stream[0], P.keys, b), philox_block(stream[1], P.keys, b), c, z);
+      const PhiloxBlockPart U = philox_block_part(fam, b);  // shared by both streams
+      scaled_tnormals_x2<kRepLog>(T, philox_block(P.keys, stream[0], U), philox_block(P.keys, stream[1], U), c, z);
       em_block4_2(Y, comp, a2, negK4, z);
     }
     float2 z[4];
-    scaled_normals_x2(philox_block(stream[0], P.keys, b), philox_block(stream[1], P.keys, b), c, z);
+    const PhiloxBlockPart U = philox_block_part(fam, b);
+    scaled_tnormals_x2<kRepLog>(T, philox_block(P.keys, stream[0], U), philox_block(P.keys, stream[1], U), c, z);
     ++b;
     float Ys[2] = {Y.x, Y.y}, Cs[2] = {comp.x, comp.y};
 #pragma unroll

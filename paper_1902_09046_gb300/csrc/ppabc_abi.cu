@@ -123,18 +123,20 @@ int ppabc_philox_raw(uint64_t seed, const uint32_t* ctr, uint64_t n, uint32_t* o
 }
 
 int ppabc_normals(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t tag, uint64_t j0, uint64_t n,
-                  float* z, void* stream) {
+                  uint32_t method, float* z, void* stream) {
+  if (method > PPABC_BM_TABLE) return set_error(PPABC_EINVAL, "method must be PPABC_BM_POLY or PPABC_BM_TABLE");
   if (n == 0) return PPABC_OK;
   if (!z) return set_error(PPABC_EINVAL, "z must be non-NULL");
   if (j0 + n < j0 || ((j0 + n - 1) >> 2) > 0xFFFFFFFFull)
     return set_error(PPABC_EINVAL, "normal index range exceeds 2^34");
   int rc = require_device();
   if (rc) return rc;
-  return check_cuda(launch_normals(seed, c1, c2, tag, j0, n, z, static_cast<cudaStream_t>(stream)),
+  return check_cuda(launch_normals(seed, c1, c2, tag, j0, n, method, z, static_cast<cudaStream_t>(stream)),
                     "normals launch");
 }
 
-int ppabc_box_muller(const uint32_t* w, uint64_t n, float* z, void* stream) {
+int ppabc_box_muller(const uint32_t* w, uint64_t n, uint32_t method, float* z, void* stream) {
+  if (method > PPABC_BM_TABLE) return set_error(PPABC_EINVAL, "method must be PPABC_BM_POLY or PPABC_BM_TABLE");
   if (n == 0) return PPABC_OK;
   if (!w || !z) return set_error(PPABC_EINVAL, "w and z must be non-NULL");
   if ((reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(z)) & 7u)
@@ -142,7 +144,7 @@ int ppabc_box_muller(const uint32_t* w, uint64_t n, float* z, void* stream) {
   if (n > 0x7FFFFFFFull * 256ull) return set_error(PPABC_EINVAL, "n too large");
   int rc = require_device();
   if (rc) return rc;
-  return check_cuda(launch_box_muller(w, n, z, static_cast<cudaStream_t>(stream)), "box_muller launch");
+  return check_cuda(launch_box_muller(w, n, method, z, static_cast<cudaStream_t>(stream)), "box_muller launch");
 }
 
 int abc_prior_predictive(const ppabc_ou_model* h_model, const double* h_y_obs, uint64_t n_samples,

@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(kTgThreads) toggle_abc(const __grid_constant__
   const uint32_t i = blockIdx.x;
   const uint32_t g = base + i;
   // Prior draw (every thread draws the same theta from the sample's counter).
-  const uint4 w0 = philox4x32_10(make_uint4(0u, g, P.sub, kTagTogglePrior), P.keys);
-  const uint4 w1 = philox4x32_10(make_uint4(1u, g, P.sub, kTagTogglePrior), P.keys);
+  const uint4 w0 = philox4x32_10(make_uint4(kTagTogglePrior, 0u, P.sub, g), P.keys);
+  const uint4 w1 = philox4x32_10(make_uint4(kTagTogglePrior, 1u, P.sub, g), P.keys);
   const uint32_t words[7] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z};
   float th[7];
 #pragma unroll
@@ -118,25 +118,29 @@ __global__ void __launch_bounds__(kTgThreads) toggle_abc(const __grid_constant__
   const float alpha_u = th[3], alpha_v = th[4], beta_u = th[5], beta_v = th[6];
   const uint32_t T = P.T, C = P.C;
   const uint32_t tag = (P.sub << 8) | kTagTogglePath;
+  // the cells of a sample are the streams of one family (substream = g)
+  const PhiloxFamily fam = philox_family(P.keys, tag, g);
   const uint32_t steps = T - 1;
   // Cells c0 and c0 + kTgThreads run together, packed (lane q = cell q): the
   // same cells per thread as one at a time, with two independent chains.
   for (uint32_t c0 = threadIdx.x; c0 < C; c0 += 2 * kTgThreads) {
     const uint32_t c1 = c0 + kTgThreads;
     const bool has1 = c1 < C;
-    const PhiloxStream S0 = philox_stream(P.keys, g, c0, tag);
-    const PhiloxStream S1 = philox_stream(P.keys, g, has1 ? c1 : c0, tag);
+    const PhiloxStream S0 = philox_stream(P.keys, fam, c0);
+    const PhiloxStream S1 = philox_stream(P.keys, fam, has1 ? c1 : c0);
     float2 U = splat2(10.0f), V = splat2(10.0f);
     // normals 2(j-1), 2(j-1)+1 drive step j: one counter block covers two steps
     uint32_t b = 0;
     uint32_t j = 0;
     float2 z[4];
     for (; j + 2 <= steps; j += 2, ++b) {
-      normals_x2(philox_block(S0, P.keys, b), philox_block(S1, P.keys, b), z);
+      const PhiloxBlockPart Ub = philox_block_part(fam, b);
+      normals_x2(philox_block(P.keys, S0, Ub), philox_block(P.keys, S1, Ub), z);
       toggle_step2(U, V, z[0], z[1], beta_u, beta_v, alpha_u, alpha_v);
       toggle_step2(U, V, z[2], z[3], beta_u, beta_v, alpha_u, alpha_v);
     }
-    normals_x2(philox_block(S0, P.keys, b), philox_block(S1, P.keys, b), z);
+    const PhiloxBlockPart Ub = philox_block_part(fam, b);
+    normals_x2(philox_block(P.keys, S0, Ub), philox_block(P.keys, S1, Ub), z);
     float2 eta;
     if (j < steps) {  // odd number of steps: one more, eta is normal 2 of this block
       toggle_step2(U, V, z[0], z[1], beta_u, beta_v, alpha_u, alpha_v);

@@ -27,14 +27,16 @@ __device__ __forceinline__ void kahan_add2(float2& s, float2& comp, float2 x) {
 __device__ __forceinline__ double2 dataset_ybar2(const PhiloxKeys& K, double lam, uint32_t n_obs,
                                                  double inv_n, uint32_t c1a, uint32_t c1b, uint32_t c2,
                                                  uint32_t tag) {
-  const PhiloxStream S0 = philox_stream(K, c1a, c2, tag);
-  const PhiloxStream S1 = philox_stream(K, c1b, c2, tag);
+  const PhiloxFamily F = philox_family(K, tag, c2);
+  const PhiloxStream S0 = philox_stream(K, F, c1a);
+  const PhiloxStream S1 = philox_stream(K, F, c1b);
   const uint32_t n_full = (n_obs + 1) >> 2;
   const uint32_t rem = (n_obs + 1) & 3u;
   float2 z0 = splat2(0.0f), s = splat2(0.0f), comp = splat2(0.0f);
   float2 z[4];
   for (uint32_t b = 0; b < n_full; ++b) {
-    normals_x2(philox_block(S0, K, b), philox_block(S1, K, b), z);
+    const PhiloxBlockPart U = philox_block_part(F, b);
+    normals_x2(philox_block(K, S0, U), philox_block(K, S1, U), z);
     // a block's normals summed pairwise, then one compensated add
     if (b == 0) {
       z0 = z[0];
@@ -44,7 +46,8 @@ __device__ __forceinline__ double2 dataset_ybar2(const PhiloxKeys& K, double lam
     }
   }
   if (rem) {
-    normals_x2(philox_block(S0, K, n_full), philox_block(S1, K, n_full), z);
+    const PhiloxBlockPart U = philox_block_part(F, n_full);
+    normals_x2(philox_block(K, S0, U), philox_block(K, S1, U), z);
     if (n_full == 0) {
       z0 = z[0];
     } else {

@@ -44,5 +44,8 @@ def test_committed_profiles_match_the_kernel_sources():
     assert traffic["source_hash"] == bench.kernel_source_hash()
     pb = bench.pipe_bounds(200.0, 16777216 * 10000)
     assert pb is not None and pb["binding"] in ("issue", "alu", "fma", "fmaheavy")
-    assert bench.profiled_traffic(16777216) == pytest.approx(traffic["dram_bytes"])
+    if traffic["dram_bytes"] is None:  # the kernel changed since the last full-size DRAM capture
+        assert bench.profiled_traffic(16777216) is None
+    else:
+        assert bench.profiled_traffic(16777216) == pytest.approx(traffic["dram_bytes"])
     assert bench.bege_profile(60.0, 1024 * 1099) is not None

@@ -52,7 +52,7 @@ def _same(a, b):
     np.testing.assert_array_equal(to_np(a["post"]), to_np(b["post"]))
 
 
-@pytest.mark.parametrize("tile", [(128, 4096), (256, 1024), (128, 1)])
+@pytest.mark.parametrize("tile", [(512, 4096), (256, 1024), (512, 1)])
 def test_batched_equals_alone(tile):
     binding = require_gpu()
     jobs = _mix()
@@ -73,7 +73,7 @@ def test_batched_equals_alone(tile):
 def test_graph_replay_is_identical():
     binding = require_gpu()
     jobs = _mix()
-    b = binding.Batch(jobs, tile=(128, 4096))
+    b = binding.Batch(jobs, tile=(512, 4096))
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         b.launch(graph=True, stream=s)

@@ -86,8 +86,9 @@ def test_philox_key_and_counter_all_matter():
 
 def _words(n_blocks, seed=99):
     ctr = np.zeros((n_blocks, 4), dtype=np.uint32)
-    ctr[:, 0] = np.arange(n_blocks, dtype=np.uint32)
-    ctr[:, 3] = 1
+    # blocks 0..n_blocks-1 of the stream (index 0, substream 0, tag PATH)
+    ctr[:, 1] = np.arange(n_blocks, dtype=np.uint32)
+    ctr[:, 0] = 1
     return oracle.philox(seed, ctr).reshape(-1)
 
 
