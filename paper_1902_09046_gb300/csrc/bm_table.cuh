@@ -10,10 +10,10 @@
 //  * -2 ln u by Tang's table-driven method (ACM TOMS 16(4), 1990): u = 2^e f
 //    with f in [3/4, 3/2), bucket j = the top 8 bits of f's field, r =
 //    fma(f, c_j, -1) with |r| <= 2^-9, t = -2 r + r^2 (1 - 2r/3) for
-//    -2 log1p(r), and -2 ln u = fma(e, K_hi, A_j + fma(e, K_lo, t)), where
-//    A_j = 2 ln c_j (c_j chosen by Gal's accurate-table method so that A_j is
-//    within 2^-12 ulp of its binary32 value) and K_hi + K_lo = -2 ln 2.
-//    Within 0.95 ulp on all 2^23 inputs.
+//    -2 log1p(r), and -2 ln u = fma(e, K, A_j + t), where A_j = 2 ln c_j
+//    (c_j chosen by Gal's accurate-table method so that A_j is within 2^-12
+//    ulp of its binary32 value) and K = RN(-2 ln 2).  Within 0.95 ulp on all
+//    2^23 inputs.
 //  * (cos, sin)(2 pi u): m = 2^11 i + k, 2 pi u = a_i + b_k with a_i =
 //    2 pi i / 4096 and b_k = 2 pi (k + 1/2) 2^-23, and
 //      cos = C_i + fma(C_i, cm_k, -S_i s_k),  sin = S_i + fma(S_i, cm_k, C_i s_k)
@@ -118,8 +118,7 @@ __device__ __forceinline__ float neg2_log_tab(const BmTab& T, uint32_t w) {
   const float r = fmaf(f, cA.x, -1.0f);
   const float q = fmaf(r, -0x1.555556p-1f, 1.0f);
   const float t = fmaf(r * q, r, -2.0f * r);
-  const float v = fmaf(ef, __uint_as_float(kBmLogKLo), t);
-  return fmaf(ef, __uint_as_float(kBmLogKHi), cA.y + v);
+  return fmaf(ef, __uint_as_float(kBmLogK), cA.y + t);
 }
 
 // (sin, cos)(2 pi u(w)): C, S from entry w >> 20 of the 4096-entry table,
@@ -161,8 +160,7 @@ __device__ __forceinline__ float2 neg2_log_tab2(const BmTab& T, uint32_t wa, uin
   const float2 r = make_float2(fmaf(fa, ca.x, -1.0f), fmaf(fb, cb.x, -1.0f));
   const float2 q = fma2(r, splat2(-0x1.555556p-1f), splat2(1.0f));
   const float2 t = fma2(mul2(r, q), r, mul2(splat2(-2.0f), r));
-  const float2 v = fma2(ef, splat2(__uint_as_float(kBmLogKLo)), t);
-  return fma2(ef, splat2(__uint_as_float(kBmLogKHi)), make_float2(ca.y + v.x, cb.y + v.y));
+  return fma2(ef, splat2(__uint_as_float(kBmLogK)), make_float2(ca.y + t.x, cb.y + t.y));
 }
 
 // The four normals of one counter block, the two radii side by side, the

@@ -126,7 +126,9 @@ __global__ void __launch_bounds__(kPipeThreads) em_ou_pipe(const __grid_constant
   double acc = 0.0;
   const Em4 E4 = em4_constants(k);
   uint32_t s = 0, b = 0, j = 0, s_next = 0, b_end = 0;
-  bool seg = true;  // a new run of whole blocks starts at block b
+  bool seg = true;       // a new run of whole blocks starts at block b
+  bool pending = false;  // zp holds the first block of a pair of the run
+  float4 zp = make_float4(0.f, 0.f, 0.f, 0.f);
   for (uint32_t r = 0; r <= rounds; ++r) {
     if (r > 0) {
       for (uint32_t q = 0; q < static_cast<uint32_t>(kPipeRound) && j < n_obs; ++q) {
@@ -138,8 +140,16 @@ __global__ void __launch_bounds__(kPipeThreads) em_ou_pipe(const __grid_constant
           s += (b_end - b) << 2;
           seg = false;
         }
-        if (b < b_end) {
-          em_block4(Y, comp, E4, z);
+        if (b < b_end) {  // the run's blocks in pairs, an odd last one alone (as ou_path)
+          if (pending) {
+            em_block8(Y, comp, E4, zp, z);
+            pending = false;
+          } else if (b + 1 < b_end) {
+            zp = z;
+            pending = true;
+          } else {
+            em_block4(Y, comp, E4, z);
+          }
           ++b;
           continue;
         }

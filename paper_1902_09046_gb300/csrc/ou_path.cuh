@@ -68,17 +68,25 @@ __device__ __forceinline__ void em_step(float& Y, float& comp, float k, float cz
 // where K4 comes from binary64 (a^4 itself is too close to 1 to carry the
 // mean reversion in binary32).  Same mathematics as four em_step calls, with
 // one rounding of the state instead of four.
+//
+// Runs of whole blocks are taken two blocks (eight steps) at a time, with
+//   inc = -K8 Y + (..((a cz_0 + cz_1) a + cz_2) a + .. ) a + cz_7,  K8 = 1 - a^8,
+// and an odd last block of a run alone; every kernel groups the blocks of a
+// run the same way, so their results stay bit-identical.
 struct Em4 {
   float a;   // 1 - k, binary32
   float K4;  // 1 - a^4 from binary64
+  float K8;  // 1 - a^8 from binary64
 };
 
 __device__ __forceinline__ Em4 em4_constants(float k) {
   const double ad = 1.0 - static_cast<double>(k);
   const double a2 = ad * ad;
+  const double a4 = a2 * a2;
   Em4 E;
   E.a = static_cast<float>(ad);
-  E.K4 = static_cast<float>(1.0 - a2 * a2);
+  E.K4 = static_cast<float>(1.0 - a4);
+  E.K8 = static_cast<float>(1.0 - a4 * a4);
   return E;
 }
 
@@ -90,12 +98,33 @@ __device__ __forceinline__ void em_block4(float& Y, float& comp, const Em4& E, f
   Y = t;
 }
 
+// Two consecutive blocks (eight steps) as one compensated update.
+__device__ __forceinline__ void em_block8(float& Y, float& comp, const Em4& E, float4 c0, float4 c1) {
+  float s8 = fmaf(fmaf(fmaf(E.a, c0.x, c0.y), E.a, c0.z), E.a, c0.w);
+  s8 = fmaf(fmaf(fmaf(fmaf(s8, E.a, c1.x), E.a, c1.y), E.a, c1.z), E.a, c1.w);
+  const float y = fmaf(-E.K8, Y, s8) - comp;
+  const float t = Y + y;
+  comp = (t - Y) - y;
+  Y = t;
+}
+
 // em_block4 on two samples at once (lane q is sample q), with the same
 // operations in the same order: each lane is bit for bit em_block4's result.
 // x - y is formed as fma(y, -1, x), which rounds identically.
 __device__ __forceinline__ void em_block4_2(float2& Y, float2& comp, float2 a, float2 negK4, const float2 z[4]) {
   const float2 s4 = fma2(fma2(fma2(a, z[0], z[1]), a, z[2]), a, z[3]);
   const float2 y = fma2(comp, splat2(-1.0f), fma2(negK4, Y, s4));
+  const float2 t = add2(Y, y);
+  comp = fma2(y, splat2(-1.0f), fma2(Y, splat2(-1.0f), t));
+  Y = t;
+}
+
+// em_block8 on two samples at once, the same operations in the same order.
+__device__ __forceinline__ void em_block8_2(float2& Y, float2& comp, float2 a, float2 negK8, const float2 z0[4],
+                                            const float2 z1[4]) {
+  float2 s8 = fma2(fma2(fma2(a, z0[0], z0[1]), a, z0[2]), a, z0[3]);
+  s8 = fma2(fma2(fma2(fma2(s8, a, z1[0]), a, z1[1]), a, z1[2]), a, z1[3]);
+  const float2 y = fma2(comp, splat2(-1.0f), fma2(negK8, Y, s8));
   const float2 t = add2(Y, y);
   comp = fma2(y, splat2(-1.0f), fma2(Y, splat2(-1.0f), t));
   Y = t;
@@ -135,8 +164,15 @@ __device__ __forceinline__ double ou_path(const OUConst& P, const BmTab& T, uint
     const uint32_t b_end = b + (s_next > s + 4u ? (s_next - s - 1u) >> 2 : 0u);
     s += (b_end - b) << 2;
 #pragma unroll 2
-    for (; b < b_end; ++b)
+    for (; b + 1 < b_end; b += 2) {
+      const float4 z0 = scaled_tnormals_of<kRepLog>(T, philox_block(P.keys, fam, stream, b), c);
+      const float4 z1 = scaled_tnormals_of<kRepLog>(T, philox_block(P.keys, fam, stream, b + 1), c);
+      em_block8(Y, comp, E4, z0, z1);
+    }
+    if (b < b_end) {
       em_block4(Y, comp, E4, scaled_tnormals_of<kRepLog>(T, philox_block(P.keys, fam, stream, b), c));
+      ++b;
+    }
     // The block holding step s_next (and possibly later observation steps).
     const float4 z = scaled_tnormals_of<kRepLog>(T, philox_block(P.keys, fam, stream, b), c);
     ++b;
@@ -190,6 +226,7 @@ __device__ __forceinline__ void ou_path2(const OUConst& P, const BmTab& T, const
   const float2 c = make_float2(th3[0] * P.sqrt_dt, th3[1] * P.sqrt_dt);
   const float2 a2 = make_float2(E4[0].a, E4[1].a);
   const float2 negK4 = make_float2(-E4[0].K4, -E4[1].K4);
+  const float2 negK8 = make_float2(-E4[0].K8, -E4[1].K8);
   float2 Y = make_float2(Y0[0], Y0[1]), comp = make_float2(comp0[0], comp0[1]);
   const uint32_t S = P.n_steps;
   const uint32_t n_obs = P.n_obs;
@@ -198,11 +235,20 @@ __device__ __forceinline__ void ou_path2(const OUConst& P, const BmTab& T, const
     uint32_t s_next = P.s_obs[j];
     const uint32_t b_end = b + (s_next > s + 4u ? (s_next - s - 1u) >> 2 : 0u);
     s += (b_end - b) << 2;
-    for (; b < b_end; ++b) {
+    for (; b + 1 < b_end; b += 2) {
+      float2 z0[4], z1[4];
+      const PhiloxBlockPart U0 = philox_block_part(fam, b);  // shared by both streams
+      scaled_tnormals_x2<kRepLog>(T, philox_block(P.keys, stream[0], U0), philox_block(P.keys, stream[1], U0), c, z0);
+      const PhiloxBlockPart U1 = philox_block_part(fam, b + 1);
+      scaled_tnormals_x2<kRepLog>(T, philox_block(P.keys, stream[0], U1), philox_block(P.keys, stream[1], U1), c, z1);
+      em_block8_2(Y, comp, a2, negK8, z0, z1);
+    }
+    if (b < b_end) {
       float2 z[4];
-      const PhiloxBlockPart U = philox_block_part(fam, b);  // shared by both streams
+      const PhiloxBlockPart U = philox_block_part(fam, b);
       scaled_tnormals_x2<kRepLog>(T, philox_block(P.keys, stream[0], U), philox_block(P.keys, stream[1], U), c, z);
       em_block4_2(Y, comp, a2, negK4, z);
+      ++b;
     }
     float2 z[4];
     const PhiloxBlockPart U = philox_block_part(fam, b);
