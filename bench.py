@@ -36,8 +36,6 @@ from paper_1902_09046_gb300 import workloads  # noqa: E402
 
 METRIC = "EM path-steps/sec (+ frac of FP32/MUFU roofline)"
 UNIT = "path-steps/s"
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
 MUFU_PER_SM_CLK = 16          # special-function (MUFU) lanes per SM per clock
 MUFU_PER_PATH_STEP = 2.0      # log, sqrt, sin, cos per Box-Muller pair = 2 per normal
 KERNEL_SOURCES = ("paper_1902_09046_gb300/csrc/em_ou.cu", "paper_1902_09046_gb300/csrc/ou_path.cuh",
@@ -62,6 +60,11 @@ def parse_args():
     ap.add_argument("--abc-steps", type=int, default=10_000)
     ap.add_argument("--pv-sets", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-latency", action="store_true",
+                    help="skip the batched-vs-plain and served-vs-plain blocks of the default run")
+    ap.add_argument("--batch-repeats", type=int, default=10)
+    ap.add_argument("--latency-serve-seconds", type=float, default=10.0,
+                    help="length of the served-vs-plain replay in the default run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -86,12 +89,13 @@ def path_steps_per_step(abc, pv):
     return abc_steps, pv_steps
 
 
-def config_dict(abc, pv, world):
+def config_dict(abc, pv, world, k_accept=None):
+    k = abc.k_accept if k_accept is None else k_accept
     return {
         "workload": (f"ou_abc N={abc.n_samples} S={abc.model['n_steps']} dt={abc.model['dt']:g} "
-                     f"k={abc.k_accept} + pvalue K={len(pv.lambdas)} M={pv.m_sets} n={pv.n_obs}"),
+                     f"k={k} + pvalue K={len(pv.lambdas)} M={pv.m_sets} n={pv.n_obs}"),
         "abc_samples_per_rank": abc.n_samples, "em_steps": abc.model["n_steps"],
-        "k_accept": abc.k_accept, "pvalue_lambdas": len(pv.lambdas), "pvalue_sets": pv.m_sets,
+        "k_accept": k, "pvalue_lambdas": len(pv.lambdas), "pvalue_sets": pv.m_sets,
         "pvalue_n": pv.n_obs, "sharding": f"sample and data-set ranges over {world} rank(s)",
         "l2": "flushed between timed steps (256 MiB write)",
     }
@@ -252,7 +256,14 @@ def profiled_traffic(n_samples):
     return float(rec["dram_bytes"]) * n_samples / float(rec["n_samples"])
 
 
-def pipe_bounds(ms_per_launch, path_steps):
+def device_props(binding):
+    """SM count and maximum SM clock of the current device, read at run time
+    (the roofline and the pipe ceilings are built from them)."""
+    sms, mhz = binding.device_info()
+    return {"sm_count": int(sms), "sm_max_mhz": float(mhz)}
+
+
+def pipe_bounds(ms_per_launch, path_steps, dev):
     """The per-pipe ceilings of the kernel from its measured cycles per warp
     step (32 path-steps) on one SM sub-partition -- issue slots, ALU-pipe
     cycles, FMA-pipe cycles, cycles of its heavy sub-pipe -- read from the
@@ -268,7 +279,7 @@ def pipe_bounds(ms_per_launch, path_steps):
     if not cyc or rec.get("source_hash") != kernel_source_hash():
         return None
     achieved = path_steps / (ms_per_launch / 1e3)
-    smsp_cycles_per_s = SM_COUNT * 4 * SM_MAX_MHZ * 1e6
+    smsp_cycles_per_s = dev["sm_count"] * 4 * dev["sm_max_mhz"] * 1e6
     out = {"cycles_per_warp_step": cyc}
     for name, c in cyc.items():
         if name == "elapsed":
@@ -293,6 +304,7 @@ def gpu_arm(args):
         dist.init_process_group("nccl")
     libbuild.build()
     binding.device_check()
+    dev_props = device_props(binding)
     abc, pv = workload_config(args)
     N = abc.n_samples
     base = rank * N
@@ -307,15 +319,22 @@ def gpu_arm(args):
     lam_dev = lam_host.to(dev)
     dist_buf = torch.empty(N, dtype=torch.float64, device=dev)
     ws = torch.empty(binding.abc_select_workspace_bytes(N), dtype=torch.uint8, device=dev)
-    sel_out = {"idx": torch.empty(abc.k_accept, dtype=torch.uint32, device=dev),
-               "rec": torch.empty((abc.k_accept, 4), dtype=torch.float32, device=dev),
+    # One job of N x world samples: each rank keeps its own k nearest of the
+    # global k (k_local = min(k, N)); with world > 1 the ranks then merge
+    # their candidates (shard.merge_topk over NCCL) into the global accepted
+    # set, and all-reduce the p-value tail counts.
+    k_global = max(1, int(0.001 * N * world))
+    k_local = min(k_global, N)
+    sel_out = {"idx": torch.empty(k_local, dtype=torch.uint32, device=dev),
+               "rec": torch.empty((k_local, 4), dtype=torch.float32, device=dev),
                "n_acc": torch.empty(1, dtype=torch.uint64, device=dev),
                "eps": torch.empty(1, dtype=torch.float64, device=dev),
                "post": torch.empty(6, dtype=torch.float64, device=dev)}
     pv_out = {"counts": torch.empty(len(pv.lambdas), dtype=torch.uint64, device=dev),
               "p": torch.empty(len(pv.lambdas), dtype=torch.float64, device=dev)}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    launches_per_step = 1 + 11 + 2
+    launches_per_step = 1 + 11 + 2 + (2 + 12 if world > 1 else 0)
+    merged = {}
 
     def step(em_events=None):
         if em_events is not None:
@@ -324,10 +343,15 @@ def gpu_arm(args):
                                      want_theta=False, out={"dist": dist_buf}, stream=stream)
         if em_events is not None:
             em_events[1].record(stream)
-        binding.abc_select(dist_buf, k=abc.k_accept, model=abc.model, seed=abc.seed, sample_base=base,
+        binding.abc_select(dist_buf, k=k_local, model=abc.model, seed=abc.seed, sample_base=base,
                            workspace=ws, out=sel_out, stream=stream)
         binding.pvalue_sweep(lam_dev, pv.n_obs, pv.m_sets, pv.ybar_obs, pv.seed, set_base=set_base,
                              out=pv_out, stream=stream)
+        if world > 1:
+            from paper_1902_09046_gb300 import shard
+            cand = binding.abc_select_candidates(dist_buf, sel_out, k_local, sample_base=base, stream=stream)
+            merged.update(shard.merge_topk(cand, k_global))
+            merged["counts"] = shard.allreduce_counts(pv_out["counts"], pv.m_sets)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -398,27 +422,45 @@ def gpu_arm(args):
 
     # Roofline of the dominant kernel (em_ou_fused): 2 MUFU-class operations
     # (log, sqrt, sin, cos per Box-Muller pair) per path-step against 16 MUFU
-    # lanes per SM per clock on 152 SMs at the 2070 MHz maximum clock.
+    # lanes per SM per clock on the device's SMs at its maximum SM clock.
     em_avg_s = statistics.mean(em_ms) / 1e3
     achieved = abc_steps / em_avg_s / 1e9
-    peak = SM_COUNT * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / MUFU_PER_PATH_STEP / 1e9
+    peak = (dev_props["sm_count"] * MUFU_PER_SM_CLK * dev_props["sm_max_mhz"] * 1e6
+            / MUFU_PER_PATH_STEP / 1e9)
     roof = {"kernel": "em_ou_fused_x2", "bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "Gpath-steps/s", "frac": achieved / peak, "traffic": profiled_traffic(N),
-            "peak_basis": "FP32+MUFU roofline: 2 MUFU ops/path-step (log,sqrt,sin,cos per pair), "
-                          "16 MUFU/SM/clk x 152 SMs x 2070 MHz; FP32 pipe bound (6 ops/step, "
-                          "128/SM/clk) is looser",
-            "pipe_bounds": pipe_bounds(statistics.mean(em_ms), abc_steps)}
+            "peak_basis": (f"FP32+MUFU roofline: 2 MUFU ops/path-step (log,sqrt,sin,cos per pair), "
+                           f"16 MUFU/SM/clk x {dev_props['sm_count']} SMs x {dev_props['sm_max_mhz']:g} MHz "
+                           "(read from the device); FP32 pipe bound (6 ops/step, 128/SM/clk) is looser"),
+            "pipe_bounds": pipe_bounds(statistics.mean(em_ms), abc_steps, dev_props)}
     clock = clocks.summary()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded)", "config": config_dict(abc, pv, world),
+            "data": "synthetic (seeded)", "config": config_dict(abc, pv, world, k_global),
             "parts": {"em_ms_per_step": statistics.mean(em_ms),
                       "abc_path_steps": abc_steps, "pvalue_path_steps": pv_steps},
-            "roofline": roof, "clocks": clock,
+            "roofline": roof, "clocks": clock, "device": dev_props,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps}
+    if world > 1:
+        line["merge"] = {"k_global": k_global, "k_local": k_local,
+                         "global_eps": float(merged["eps"].item()),
+                         "global_n_acc": int(merged["n_acc"].item()),
+                         "global_posterior_mean": [float(v) for v in merged["post"][:3].tolist()],
+                         "note": "global accepted set of the N x world-sample job, merged over NCCL"}
+    if world == 1 and not args.no_latency:
+        # The latency half of the metric (BASELINE config 4, shortened replay)
+        # and the batched-vs-plain form (config 3), each with its clocks.
+        with ClockSampler(local_rank) as c_batch:
+            batch = batch_comparison(args.jobs, args.batch_repeats)
+        batch["clocks"] = c_batch.summary()
+        with ClockSampler(local_rank) as c_serve:
+            serve = serve_comparison(args.serve_rate, args.latency_serve_seconds, args.slots)
+        serve["clocks"] = c_serve.summary()
+        line["batch"] = batch
+        line["serve"] = serve
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(abc, pv, args.cpu_seconds)
     if rank == 0:
@@ -433,17 +475,15 @@ def job_specs(jobs):
             for j in jobs]
 
 
-def batch_mode(args):
-    """256 uneven OU-ABC jobs: one job per launch pair (plain) against one
-    persistent, graph-replayed launch (batched); same results either way."""
+def batch_comparison(n_jobs, reps, clocks=None):
+    """The uneven job mix run plain (one job per launch pair, one stream) and
+    batched (one persistent, graph-replayed launch): `reps` alternating
+    repeats of each, CUDA-event timed; the two forms give the same accepted
+    sets, checked on the last repeat."""
     import torch
     from paper_1902_09046_gb300 import autotune, binding
-    from paper_1902_09046_gb300 import build as libbuild
 
-    torch.cuda.set_device(0)
-    libbuild.build()
-    binding.device_check()
-    jobs = workloads.batched_jobs(args.jobs)
+    jobs = workloads.batched_jobs(n_jobs)
     specs = job_specs(jobs)
     total_steps = sum(j.path_steps for j in jobs)
     dev = torch.device("cuda")
@@ -464,15 +504,13 @@ def batch_mode(args):
             binding.abc_select(dist[:j.n], k=j.k_accept, model=j.model, seed=j.seed,
                                workspace=ws, out=o, stream=stream)
 
-    def timed(fn, reps):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(reps)]
-        for a, b in ev:
-            a.record(stream)
-            fn()
-            b.record(stream)
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
         stream.synchronize()
-        return [a.elapsed_time(b) for a, b in ev]
+        return a.elapsed_time(b)
 
     with torch.cuda.stream(stream):
         t_tune = time.perf_counter()
@@ -482,35 +520,29 @@ def batch_mode(args):
         plain()
         batch.launch(graph=True, stream=stream)
         stream.synchronize()
-        with ClockSampler(0) as clocks:
-            ms_plain = timed(plain, args.steps)
-            ms_batch = timed(lambda: batch.launch(graph=True, stream=stream), args.steps)
-        # the two forms give identical accepted sets
+        ms_plain, ms_batch = [], []
+        for _ in range(reps):
+            ms_plain.append(timed(plain))
+            ms_batch.append(timed(lambda: batch.launch(graph=True, stream=stream)))
         same = True
         for o, r in zip(outs, batch.results()):
             same &= bool(torch.equal(o["idx"], r["idx"])) and bool(torch.equal(o["post"], r["post"]))
         batch.close()
-    plain_ms = statistics.median(ms_plain)
-    batch_ms = statistics.median(ms_batch)
-    line = {"mode": "batch", "metric": "EM path-steps/sec, batched vs plain", "unit": UNIT,
-            "value": total_steps / (batch_ms / 1e3), "plain_value": total_steps / (plain_ms / 1e3),
-            "speedup": plain_ms / batch_ms, "batch_ms": batch_ms, "plain_ms": plain_ms,
-            "path_steps": total_steps, "jobs": len(jobs), "tile": list(tile),
-            "autotune_s": t_tune, "results_identical": same, "steps": args.steps,
-            "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded)",
-            "config": {"workload": f"{len(jobs)} OU-ABC jobs, N log-uniform [1e3,1e7], "
-                                   f"S uniform {{100..10^4}}, dt=10/S, 1% accepted"},
-            "clocks": clocks.summary()}
-    print(json.dumps(line), flush=True)
-    return 0
+    ratios = [p / b for p, b in zip(ms_plain, ms_batch)]
+    plain_ms, batch_ms = statistics.median(ms_plain), statistics.median(ms_batch)
+    return {"value": total_steps / (batch_ms / 1e3), "plain_value": total_steps / (plain_ms / 1e3),
+            "unit": UNIT, "speedup_median": statistics.median(ratios), "speedup_min": min(ratios),
+            "speedup_max": max(ratios), "batch_ms": batch_ms, "plain_ms": plain_ms,
+            "batch_ms_range": [min(ms_batch), max(ms_batch)], "plain_ms_range": [min(ms_plain), max(ms_plain)],
+            "repeats": reps, "path_steps": total_steps, "jobs": len(jobs), "tile": list(tile),
+            "autotune_s": t_tune, "results_identical": same,
+            "workload": (f"{len(jobs)} OU-ABC jobs, N log-uniform [1e3,1e7], S uniform {{100..10^4}}, "
+                         "dt=10/S, 1% accepted; plain = one job per launch pair on one stream")}
 
 
-def serve_mode(args):
-    """Poisson arrivals of mixed ABC / p-value jobs replayed in real time
-    against the server with `--slots` streams (served) and with one stream
-    (plain, one job at a time); p50/p99 latency and aggregate throughput."""
-    import threading as th
-
+def batch_mode(args):
+    """256 uneven OU-ABC jobs: one job per launch pair (plain) against one
+    persistent, graph-replayed launch (batched); same results either way."""
     import torch
     from paper_1902_09046_gb300 import binding
     from paper_1902_09046_gb300 import build as libbuild
@@ -518,14 +550,32 @@ def serve_mode(args):
     torch.cuda.set_device(0)
     libbuild.build()
     binding.device_check()
-    jobs = workloads.served_jobs(rate_per_s=args.serve_rate, duration_s=args.serve_seconds)
+    with ClockSampler(0) as clocks:
+        res = batch_comparison(args.jobs, args.steps)
+    line = {"mode": "batch", "metric": "EM path-steps/sec, batched vs plain", **res,
+            "steps": args.steps, "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": res.pop("workload")}, "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def serve_comparison(rate, seconds, slots):
+    """Poisson arrivals of mixed ABC / p-value jobs replayed in real time
+    against the server with `slots` streams (served) and with one stream
+    (plain, one job at a time); p50/p99 latency and aggregate throughput of
+    each, and whether every job's result is the same in both."""
+    import threading as th
+
+    from paper_1902_09046_gb300 import binding
+
+    jobs = workloads.served_jobs(rate_per_s=rate, duration_s=seconds)
     reqs = [binding.abc_request(j.model, j.y_obs, j.n, j.k_accept, j.seed) if j.kind == "abc"
             else binding.pvalue_request(j.lam, j.n_obs, j.n, j.ybar_obs, j.seed) for j in jobs]
     total_steps = sum(j.path_steps for j in jobs)
     arena = 64 << 30
 
-    def run(slots):
-        with binding.Server(arena, n_slots=slots) as srv:
+    def run(n_slots):
+        with binding.Server(arena, n_slots=n_slots) as srv:
             # warm-up: a few jobs of each kind
             for r in reqs[:8]:
                 srv.release(srv.wait(srv.submit(r), 120.0)["job_id"])
@@ -560,19 +610,30 @@ def serve_mode(args):
                 "wall_s": t_end - t0, "all_ok": ok, "peak_arena_bytes": st["peak_arena_bytes"],
                 "results": [(r["n_acc"], r["eps"], r["count"]) for r in res]}
 
-    with ClockSampler(0) as clocks:
-        served = run(args.slots)
-        plain = run(1)
+    served = run(slots)
+    plain = run(1)
     same = served.pop("results") == plain.pop("results")
+    return {"served": served, "plain": plain, "slots": slots, "jobs": len(jobs), "path_steps": total_steps,
+            "results_identical": same, "offered_path_steps_per_s": total_steps / seconds,
+            "unit": "ms (latency), path-steps/s (throughput)",
+            "workload": (f"Poisson {rate:g}/s for {seconds:g} s, 70% OU-ABC (N log-U[1e3,1e6], S U{{100..2000}}), "
+                         "30% p-value (n=50, M log-U[1e4,1e6], lambda log-U[0.01,100]), HBM arena 64 GiB")}
+
+
+def serve_mode(args):
+    import torch
+    from paper_1902_09046_gb300 import binding
+    from paper_1902_09046_gb300 import build as libbuild
+
+    torch.cuda.set_device(0)
+    libbuild.build()
+    binding.device_check()
+    with ClockSampler(0) as clocks:
+        res = serve_comparison(args.serve_rate, args.serve_seconds, args.slots)
     line = {"mode": "serve", "metric": "p50/p99 job latency and aggregate path-steps/s, served vs plain",
-            "unit": "ms", "value": served["p99_ms"], "higher_is_better": False,
-            "served": served, "plain": plain, "slots": args.slots, "jobs": len(jobs),
-            "path_steps": total_steps, "results_identical": same,
-            "offered_path_steps_per_s": total_steps / args.serve_seconds,
-            "config": {"workload": f"Poisson {args.serve_rate:g}/s for {args.serve_seconds:g} s, 70% OU-ABC "
-                                   f"(N log-U[1e3,1e6], S U{{100..2000}}), 30% p-value (n=50, M log-U[1e4,1e6], "
-                                   f"lambda log-U[0.01,100]), HBM arena 64 GiB"},
-            "data": "synthetic (seeded)", "dtype": "f32", "clocks": clocks.summary()}
+            "value": res["served"]["p99_ms"], "higher_is_better": False, **res,
+            "config": {"workload": res.pop("workload")}, "data": "synthetic (seeded)", "dtype": "f32",
+            "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -591,6 +652,7 @@ def toggle_mode(args):
     torch.cuda.set_device(0)
     libbuild.build()
     binding.device_check()
+    dev_props = device_props(binding)
     N, model = 8064, workloads.toggle_model()
     q = workloads.toggle_observed_quantiles()
     cell_steps = N * model["C"] * (model["T"] - 1)
@@ -610,19 +672,20 @@ def toggle_mode(args):
     # Roofline: per cell-step the method needs 2 normals (1 Box-Muller pair: log, sqrt, sin,
     # cos = 4 MUFU-class operations) and 2 powers (log2 + exp2 each) and 2 divisions
     # (reciprocal each): 10 MUFU-class operations at 16 per SM per clock.
-    peak = SM_COUNT * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 10.0 / 1e9
+    peak = dev_props["sm_count"] * MUFU_PER_SM_CLK * dev_props["sm_max_mhz"] * 1e6 / 10.0 / 1e9
     achieved = cell_steps / (ms / 1e3) / 1e9
     line = {"mode": "toggle", "metric": "toggle-switch prior-predictive cell-steps/s",
             "roofline": {"kernel": "toggle_abc", "bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "Gcell-steps/s", "frac": achieved / peak,
-                         "peak_basis": "10 MUFU-class ops per cell-step (Box-Muller pair 4, two "
-                                       "powers 4, two divisions 2) at 16/SM/clk x 152 SMs x 2070 MHz"},
+                         "peak_basis": ("10 MUFU-class ops per cell-step (Box-Muller pair 4, two "
+                                        f"powers 4, two divisions 2) at 16/SM/clk x {dev_props['sm_count']} SMs x "
+                                        f"{dev_props['sm_max_mhz']:g} MHz")},
             "unit": "cell-steps/s", "value": cell_steps / (ms / 1e3), "ms_per_run": ms,
             "higher_is_better": True, "vs_baseline": (PAPER_TOGGLE_SECONDS * 1e3) / ms,
             "baseline": "paper Table A.1: 69 s for this workload, C with AVX-512, 16 cores",
             "dtype": "f32", "data": "synthetic (seeded)", "steps": args.steps,
             "config": {"workload": "toggle switch N=8064 T=600 C=8000, 19 quantiles + distance"},
-            "clocks": clocks.summary()}
+            "clocks": clocks.summary(), "device": dev_props}
     if not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -641,7 +704,7 @@ def toggle_mode(args):
 
 
 
-def bege_profile(launch_ms, particle_steps):
+def bege_profile(launch_ms, particle_steps, dev):
     """Per-pipe ceilings of bege_density from its measured cycles per
     particle-step on one SM sub-partition (issue slots, FMA pipe and its heavy
     half, ALU pipe), read from the committed ncu summary, with the achieved
@@ -659,7 +722,7 @@ def bege_profile(launch_ms, particle_steps):
     if rec.get("source_hash") != h.hexdigest()[:16] or not cyc:
         return None
     achieved = particle_steps / (launch_ms / 1e3)
-    smsp_cycles_per_s = SM_COUNT * 4 * SM_MAX_MHZ * 1e6
+    smsp_cycles_per_s = dev["sm_count"] * 4 * dev["sm_max_mhz"] * 1e6
     out = {"cycles_per_particle_step": cyc}
     for name, c in cyc.items():
         if name == "elapsed":
@@ -687,6 +750,7 @@ def bege_mode(args):
     torch.cuda.set_device(0)
     libbuild.build()
     binding.device_check()
+    dev_props = device_props(binding)
     r_np = workloads.bege_returns()
     T, n_p, h = len(r_np), workloads.BEGE_N_PARTICLES, workloads.BEGE_H
     sets = {"later": workloads.bege_particles(n_p, seed=6, centre=workloads.BEGE_THETA_REF, rel_spread=0.05),
@@ -713,14 +777,15 @@ def bege_mode(args):
             res[name] = {"ms": ms, "particle_steps_per_s": n_p * T / (ms / 1e3),
                          "finite": int(np.isfinite(ll).sum())}
     main = res["later"]
-    prof = bege_profile(main["ms"], n_p * T)
+    prof = bege_profile(main["ms"], n_p * T, dev_props)
     if prof:
         bind = prof[prof["binding"]]
         roof = {"kernel": "bege_density", "bound": "alu", "unit": "particle-steps/s",
                 "achieved": main["particle_steps_per_s"], "peak": bind["ceiling_particle_steps_per_s"],
                 "frac": bind["frac"], "traffic": None, "pipe_bounds": prof,
-                "peak_basis": (f"{prof['binding']} ceiling: 152 SMs x 4 sub-partitions x 2.07 GHz / "
-                               "measured cycles per particle-step (profiles/bege_density_counts.json)")}
+                "peak_basis": (f"{prof['binding']} ceiling: {dev_props['sm_count']} SMs x 4 sub-partitions x "
+                               f"{dev_props['sm_max_mhz']:g} MHz / measured cycles per particle-step "
+                               "(profiles/bege_density_counts.json)")}
     else:
         roof = {"kernel": "bege_density", "bound": "alu", "unit": "particle-steps/s",
                 "achieved": main["particle_steps_per_s"], "peak": None, "frac": None, "traffic": None,

@@ -99,6 +99,11 @@ const char *ppabc_last_error(void);
  * PPABC_ECUDA. */
 int ppabc_device_check(void);
 
+/* The current device's SM count and maximum SM clock (kHz), as the CUDA
+ * runtime reports them; the roofline figures are built from these.  Both
+ * pointers must be non-NULL (EINVAL).  No device work is enqueued. */
+int ppabc_device_info(int *sm_count, int *max_sm_clock_khz);
+
 /*
  * Raw Philox4x32-10 blocks: out[i][0..3] = philox(ctr[i][0..3], key(seed)),
  * i < n.  ctr and out are [n][4] uint32, 16-byte aligned.  Exposes the
@@ -190,6 +195,51 @@ int abc_select(const double *dist, uint64_t n, uint64_t k, double eps,
                uint64_t *n_acc_out, double *eps_out, double *post_out,
                void *workspace, size_t workspace_bytes, void *stream);
 
+/*
+ * The exchange step of a job whose samples are split over ranks in
+ * contiguous index ranges (the static split of the paper's sampler,
+ * Sec. 3.4), for the fixed-N selection of Sec. 3.1.  Each rank selects its
+ * own k nearest with abc_select; the global k nearest by (distance, index)
+ * are among those candidates, so the ranks gather them and select again.
+ *
+ * abc_select_candidates: this rank's accepted samples as a candidate record.
+ *   dist          device [n] binary64, the distances abc_select ran on.
+ *   sample_base   global index of dist[0]; sample_base + n <= 2^32.
+ *   idx, rec      device, abc_select's idx_out and rec_out (rec 16-byte
+ *                 aligned); count = how many of them to take (<= n).
+ *   cand_dist     device [count] binary64: dist[idx[i]].
+ *   cand_index    device [count] uint64: sample_base + idx[i].
+ *   cand_theta    device [3][count] binary32: the accepted theta (SoA).
+ * EINVAL on bad arguments (nothing enqueued).
+ */
+int abc_select_candidates(const double *dist, uint64_t n, uint64_t sample_base,
+                          const uint32_t *idx, const float *rec, uint64_t count,
+                          double *cand_dist, uint64_t *cand_index, float *cand_theta,
+                          void *stream);
+
+/* Bytes of scratch abc_merge_candidates needs for m candidates and k accepted. */
+size_t abc_merge_workspace_bytes(uint64_t m, uint64_t k);
+
+/*
+ * The k nearest of m gathered candidates (abc_select_candidates records of
+ * all ranks concatenated in rank order, i.e. in ascending global index), by
+ * (distance, position): the same set, epsilon and posterior moments as
+ * abc_select on the unsharded range.
+ *   cand_*        device, as written by abc_select_candidates ([m], [m], [3][m]).
+ *   k             1 <= k <= m < 2^32.
+ *   idx_out       device [k] uint64: global indices, ascending.
+ *   rec_out       device [k] float4 (theta1, theta2, theta3, rho), 16-byte aligned.
+ *   n_acc_out     device uint64 (= k); eps_out, post_out nullable device
+ *                 ([1] epsilon, [6] posterior mean and unbiased variance).
+ *   workspace     device, abc_merge_workspace_bytes(m, k), 256-byte aligned.
+ * EINVAL / ENOMEM on bad arguments or a short workspace (nothing enqueued).
+ */
+int abc_merge_candidates(const double *cand_dist, const uint64_t *cand_index,
+                         const float *cand_theta, uint64_t m, uint64_t k,
+                         uint64_t *idx_out, float *rec_out, uint64_t *n_acc_out,
+                         double *eps_out, double *post_out, void *workspace,
+                         size_t workspace_bytes, void *stream);
+
 /* Bytes of scratch abc_rejection needs for a chunk size (256-byte aligned). */
 size_t abc_rejection_workspace_bytes(uint64_t chunk);
 
@@ -258,7 +308,11 @@ int abc_recalibrate(const double *summ, const float *theta, uint64_t n, uint32_t
  *   - n must be <= PPABC_STATIC_SELECT_MAX_N; larger n gives PPABC_EINVAL.
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before
- *     any stream capture.
+ *     any stream capture.  The address stays cached for the life of the
+ *     process: cudaDeviceReset, or anything else that destroys and re-creates
+ *     the device's primary context, can move the array, and the cached
+ *     address then no longer points at it.  Do not call abc_select_static on
+ *     a device after resetting it.
  *   - Every call uses the same array and clears what must start at zero, so
  *     calls whose work overlaps on the GPU (different streams, or different
  *     host threads without ordering) race with each other; order them on one

@@ -32,9 +32,10 @@ _ERRNAMES = {PPABC_EINVAL: "EINVAL", PPABC_ENOMEM: "ENOMEM", PPABC_ECUDA: "ECUDA
              PPABC_ETIMEOUT: "ETIMEOUT", PPABC_ENODEV: "ENODEV", PPABC_ECANCELLED: "ECANCELLED"}
 
 # Every symbol include/ppabc.h declares (checked by the CPU test-suite).
-EXPORTED = ("ppabc_abi_version", "ppabc_last_error", "ppabc_device_check", "ppabc_philox_raw",
+EXPORTED = ("ppabc_abi_version", "ppabc_last_error", "ppabc_device_check", "ppabc_device_info", "ppabc_philox_raw",
             "ppabc_normals", "ppabc_box_muller", "abc_prior_predictive", "abc_select_workspace_bytes", "abc_select",
-            "abc_select_static", "pvalue_sweep", "ppabc_batch_workspace_bytes",
+            "abc_select_static", "abc_select_candidates", "abc_merge_workspace_bytes", "abc_merge_candidates",
+            "pvalue_sweep", "ppabc_batch_workspace_bytes",
             "ppabc_batch_prepare", "ppabc_batch_launch", "ppabc_batch_launch_graph",
             "ppabc_batch_plan_destroy", "ppabc_batch_run", "ppabc_server_create",
             "ppabc_server_submit", "ppabc_server_poll", "ppabc_server_wait", "ppabc_server_fetch",
@@ -157,6 +158,7 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
             "ppabc_abi_version": ([], i32),
             "ppabc_last_error": ([], ctypes.c_char_p),
             "ppabc_device_check": ([], i32),
+            "ppabc_device_info": ([ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], i32),
             "ppabc_philox_raw": ([u64, P, u64, P, P], i32),
             "ppabc_normals": ([u64, u32, u32, u32, u64, u64, u32, P, P], i32),
             "ppabc_box_muller": ([P, u64, u32, P, P], i32),
@@ -164,6 +166,9 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
             "abc_select_workspace_bytes": ([u64], sz),
             "abc_select": ([P, u64, u64, dbl, M, u64, u64, u32, P, P, P, u64, P, P, P, P, sz, P], i32),
             "abc_select_static": ([P, u64, u64, dbl, M, u64, u64, u32, P, P, P, u64, P, P, P, P], i32),
+            "abc_select_candidates": ([P, u64, u64, P, P, u64, P, P, P, P], i32),
+            "abc_merge_workspace_bytes": ([u64, u64], sz),
+            "abc_merge_candidates": ([P, P, P, u64, u64, P, P, P, P, P, P, sz, P], i32),
             "pvalue_sweep": ([P, u32, u32, u64, u64, dbl, u64, P, P, P, P], i32),
             "ppabc_batch_workspace_bytes": ([P, u32], sz),
             "ppabc_batch_prepare": ([P, u32, P, P, sz, P, ctypes.POINTER(P)], i32),
@@ -222,6 +227,13 @@ def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p | None:
 
 def device_check() -> None:
     _check(load_library().ppabc_device_check())
+
+
+def device_info() -> tuple[int, float]:
+    """(SM count, maximum SM clock in MHz) of the current device."""
+    sms, khz = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load_library().ppabc_device_info(ctypes.byref(sms), ctypes.byref(khz)))
+    return sms.value, khz.value / 1e3
 
 
 def philox_raw(seed: int, ctr: torch.Tensor, stream=None) -> torch.Tensor:
@@ -327,6 +339,43 @@ def abc_select(dist: torch.Tensor, k: int = 0, eps: float = math.inf, model: dic
                           _ptr(post), _ptr(workspace), workspace.numel() * workspace.element_size(),
                           _stream(stream)))
     return {"idx": idx[:cap], "rec": rec[:cap], "n_acc": n_acc, "eps": eps_t, "post": post}
+
+
+def abc_select_candidates(dist: torch.Tensor, sel: dict, count: int, sample_base: int = 0,
+                          stream=None) -> dict:
+    """This rank's accepted samples (abc_select's output `sel` on `dist`) as a
+    candidate record for the merge: {"dist": [count] f64, "index": [count]
+    u64 global indices, "theta": [3,count] f32}."""
+    dev = dist.device
+    cand = {"dist": torch.empty(max(count, 1), dtype=torch.float64, device=dev),
+            "index": torch.empty(max(count, 1), dtype=torch.uint64, device=dev),
+            "theta": torch.empty((3, max(count, 1)), dtype=torch.float32, device=dev)}
+    _check(load_library().abc_select_candidates(_ptr(dist), dist.shape[0], sample_base, _ptr(sel["idx"]),
+                                                _ptr(sel["rec"]), count, _ptr(cand["dist"]),
+                                                _ptr(cand["index"]), _ptr(cand["theta"]), _stream(stream)))
+    return {"dist": cand["dist"][:count], "index": cand["index"][:count],
+            "theta": cand["theta"][:, :count] if count else cand["theta"][:, :0]}
+
+
+def abc_merge_candidates(cand_dist: torch.Tensor, cand_index: torch.Tensor, cand_theta: torch.Tensor,
+                         k: int, stream=None) -> dict:
+    """The k nearest of gathered candidates (concatenated in rank order):
+    {"idx": [k] u64 global indices, "rec": [k,4] f32, "n_acc", "eps", "post"}."""
+    m = cand_dist.shape[0]
+    dev = cand_dist.device
+    theta = cand_theta.contiguous()
+    out = {"idx": torch.empty(k, dtype=torch.uint64, device=dev),
+           "rec": torch.empty((k, 4), dtype=torch.float32, device=dev),
+           "n_acc": torch.empty(1, dtype=torch.uint64, device=dev),
+           "eps": torch.empty(1, dtype=torch.float64, device=dev),
+           "post": torch.empty(6, dtype=torch.float64, device=dev)}
+    lib = load_library()
+    ws_bytes = int(lib.abc_merge_workspace_bytes(m, k))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    _check(lib.abc_merge_candidates(_ptr(cand_dist), _ptr(cand_index), _ptr(theta), m, k, _ptr(out["idx"]),
+                                    _ptr(out["rec"]), _ptr(out["n_acc"]), _ptr(out["eps"]), _ptr(out["post"]),
+                                    _ptr(ws), ws_bytes, _stream(stream)))
+    return out
 
 
 def abc_select_static(dist: torch.Tensor, k: int = 0, eps: float = math.inf,

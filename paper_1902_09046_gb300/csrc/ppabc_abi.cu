@@ -111,6 +111,15 @@ const char* ppabc_last_error(void) { return g_last_error; }
 
 int ppabc_device_check(void) { return require_device(); }
 
+int ppabc_device_info(int* sm_count, int* max_sm_clock_khz) {
+  if (!sm_count || !max_sm_clock_khz) return set_error(PPABC_EINVAL, "sm_count and max_sm_clock_khz must be non-NULL");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(max_sm_clock_khz, cudaDevAttrClockRate, dev);
+  return check_cuda(e, "device attributes");
+}
+
 int ppabc_philox_raw(uint64_t seed, const uint32_t* ctr, uint64_t n, uint32_t* out, void* stream) {
   if (n == 0) return PPABC_OK;
   if (!ctr || !out) return set_error(PPABC_EINVAL, "ctr and out must be non-NULL");

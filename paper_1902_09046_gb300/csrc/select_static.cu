@@ -24,7 +24,9 @@ std::mutex g_mu;
 void* g_scratch_ptr[kMaxDev] = {nullptr};
 
 // Device address of g_select_scratch on the current device; resolved once per
-// device (the host-side symbol is only a stand-in, not a device address).
+// device (the host-side symbol is only a stand-in, not a device address) and
+// kept for the life of the process, so a device reset, which may reload the
+// module elsewhere, leaves it stale (documented in ppabc.h).
 int scratch_for_current_device(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);

@@ -42,10 +42,11 @@ def test_committed_profiles_match_the_kernel_sources():
     import bench
     traffic = json.load(open(os.path.join(ROOT, "profiles", "em_ou_fused_traffic.json")))
     assert traffic["source_hash"] == bench.kernel_source_hash()
-    pb = bench.pipe_bounds(200.0, 16777216 * 10000)
+    gb300 = {"sm_count": 152, "sm_max_mhz": 2070.0}
+    pb = bench.pipe_bounds(200.0, 16777216 * 10000, gb300)
     assert pb is not None and pb["binding"] in ("issue", "alu", "fma", "fmaheavy")
     if traffic["dram_bytes"] is None:  # the kernel changed since the last full-size DRAM capture
         assert bench.profiled_traffic(16777216) is None
     else:
         assert bench.profiled_traffic(16777216) == pytest.approx(traffic["dram_bytes"])
-    assert bench.bege_profile(60.0, 1024 * 1099) is not None
+    assert bench.bege_profile(60.0, 1024 * 1099, gb300) is not None

@@ -425,3 +425,50 @@ def test_recalibration_ties_on_both_sides_of_the_shared_memory_limit(n):
         u_o, rc_o = oracle.recalibrate(S_np, th_np, acc_np, k)
         np.testing.assert_array_equal(to_np(rc["u"]), u_o)
         np.testing.assert_array_equal(to_np(rc["theta_rc"]), rc_o)
+
+
+# ---------------------------------------------------------------------------
+# The exchange step of a sample-sharded job, on the device
+# ---------------------------------------------------------------------------
+
+def _sharded_select(binding, d, theta, k, cuts):
+    """Per-shard abc_select + abc_select_candidates, concatenated in shard
+    order (what the all-gather delivers), then abc_merge_candidates."""
+    cands = []
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        kl = min(k, hi - lo)
+        sel = binding.abc_select(d[lo:hi], k=kl, theta=theta[:, lo:hi].contiguous())
+        cands.append(binding.abc_select_candidates(d[lo:hi], sel, kl, sample_base=lo))
+    cat = {key: torch.cat([c[key] for c in cands], dim=-1) for key in ("dist", "index", "theta")}
+    return binding.abc_merge_candidates(cat["dist"], cat["index"], cat["theta"].contiguous(), k)
+
+
+@pytest.mark.parametrize("case", ["ou_small", "ties", "large"])
+def test_sharded_merge_equals_unsharded(case):
+    binding = require_gpu()
+    rng = np.random.default_rng(21)
+    if case == "ou_small":
+        w = workloads.abc_small()
+        out = binding.abc_prior_predictive(w.model, w.y_obs, w.n_samples, w.seed, want_theta=True)
+        d, theta, k = out["dist"], out["theta"], w.k_accept
+        cuts = [0, 3001, 3050, w.n_samples]          # uneven, one shard smaller than k
+    elif case == "ties":
+        n = 20_000
+        d = torch.from_numpy(np.round(rng.exponential(size=n), 1)).cuda()   # heavy ties across shards
+        theta = torch.from_numpy(rng.random((3, n)).astype(np.float32)).cuda()
+        k, cuts = 777, [0, 5000, 12345, n]
+    else:
+        w = workloads.abc_large()
+        n = 1 << 17
+        out = binding.abc_prior_predictive(w.model, w.y_obs, n, w.seed, want_theta=True)
+        d, theta, k = out["dist"], out["theta"], int(0.001 * n)
+        cuts = [0, n // 2, n]
+    ref = binding.abc_select(d, k=k, theta=theta)
+    got = _sharded_select(binding, d, theta, k, cuts)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(to_np(got["idx"]).astype(np.int64), to_np(ref["idx"]).astype(np.int64))
+    np.testing.assert_array_equal(to_np(got["rec"]), to_np(ref["rec"]))
+    assert int(to_np(got["n_acc"])[0]) == k
+    assert to_np(got["eps"])[0] == to_np(ref["eps"])[0]
+    # the same values in the same order; the grouping of the sums may differ
+    np.testing.assert_allclose(to_np(got["post"]), to_np(ref["post"]), rtol=1e-12, atol=1e-15)
