@@ -187,6 +187,24 @@ __device__ __forceinline__ float4 scaled_tnormals_of(const BmTab& T, uint4 w, fl
 }
 
 // The four normals of blocks w0 and w1 of two streams, packed across the
+// streams: z[l] = (normal l of w0, normal l of w1), each lane bit for bit
+// tnormals_of of its stream.
+template <bool kRepLog>
+__device__ __forceinline__ void tnormals_x2(const BmTab& T, uint4 w0, uint4 w1, float2 z[4]) {
+  const float2 rA = sqrt_pos2(neg2_log_tab2<kRepLog>(T, w0.x, w1.x));
+  const float2 rB = sqrt_pos2(neg2_log_tab2<kRepLog>(T, w0.z, w1.z));
+  float s0, c0, s1, c1, s2, c2, s3, c3;
+  sincos_2pi_tab(T, w0.y, s0, c0);
+  sincos_2pi_tab(T, w1.y, s1, c1);
+  sincos_2pi_tab(T, w0.w, s2, c2);
+  sincos_2pi_tab(T, w1.w, s3, c3);
+  z[0] = mul2(rA, make_float2(c0, c1));
+  z[1] = mul2(rA, make_float2(s0, s1));
+  z[2] = mul2(rB, make_float2(c2, c3));
+  z[3] = mul2(rB, make_float2(s2, s3));
+}
+
+// The four normals of blocks w0 and w1 of two streams, packed across the
 // streams and scaled per stream: z[l] = (c.x normal l of w0, c.y normal l of
 // w1), each lane bit for bit scaled_tnormals_of of its stream.
 template <bool kRepLog>

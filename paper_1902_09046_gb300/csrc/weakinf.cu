@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(256) weakinf_ybar(const double* __restrict__ l
     const uint32_t k = static_cast<uint32_t>(kk % n_lambda);
     const uint32_t j0 = 2 * jj, j1 = j0 + 1 < N ? j0 + 1 : j0;
     const double lam = kind ? lambda0 : lambda[k];
-    const double2 yb = dataset_ybar2(K, lam, n_obs, inv_n, j0, j1, k, kind ? kTagBase : kTagPath);
+    const double2 yb = dataset_ybar2<false, false>(BmTab{}, K, lam, n_obs, inv_n, j0, j1, k,
+                                                   kind ? kTagBase : kTagPath);
     double* out = abs_out + (static_cast<size_t>(kind) * n_lambda + k) * N;
     out[j0] = fabs(yb.x);
     if (j0 + 1 < N) out[j0 + 1] = fabs(yb.y);

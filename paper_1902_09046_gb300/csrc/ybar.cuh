@@ -6,6 +6,7 @@
 // with Kahan compensation; ybar itself is binary64.
 #pragma once
 
+#include "bm_table.cuh"
 #include "rng.cuh"
 
 namespace ppabc {
@@ -16,7 +17,9 @@ namespace ppabc {
 // added with Kahan compensation on packed binary32 pairs:
 //   y = x - comp;  t = s + y;  comp = (t - s) - y;  s = t
 // (x - y formed as fma(y, -1, x), which rounds identically), then
-// ybar = lambda z_0 + (s - comp) / n in binary64.
+// ybar = lambda z_0 + (s - comp) / n in binary64.  kTable selects the
+// table-driven Box-Muller of bm_table.cuh (tables in shared memory, T) or
+// the polynomial one of rng.cuh (T unused).
 __device__ __forceinline__ void kahan_add2(float2& s, float2& comp, float2 x) {
   const float2 y = fma2(comp, splat2(-1.0f), x);
   const float2 t = add2(s, y);
@@ -24,7 +27,16 @@ __device__ __forceinline__ void kahan_add2(float2& s, float2& comp, float2 x) {
   s = t;
 }
 
-__device__ __forceinline__ double2 dataset_ybar2(const PhiloxKeys& K, double lam, uint32_t n_obs,
+template <bool kTable, bool kRepLog>
+__device__ __forceinline__ void ybar_normals_x2(const BmTab& T, uint4 w0, uint4 w1, float2 z[4]) {
+  if (kTable)
+    tnormals_x2<kRepLog>(T, w0, w1, z);
+  else
+    normals_x2(w0, w1, z);
+}
+
+template <bool kTable, bool kRepLog>
+__device__ __forceinline__ double2 dataset_ybar2(const BmTab& T, const PhiloxKeys& K, double lam, uint32_t n_obs,
                                                  double inv_n, uint32_t c1a, uint32_t c1b, uint32_t c2,
                                                  uint32_t tag) {
   const PhiloxFamily F = philox_family(K, tag, c2);
@@ -36,7 +48,7 @@ __device__ __forceinline__ double2 dataset_ybar2(const PhiloxKeys& K, double lam
   float2 z[4];
   for (uint32_t b = 0; b < n_full; ++b) {
     const PhiloxBlockPart U = philox_block_part(F, b);
-    normals_x2(philox_block(K, S0, U), philox_block(K, S1, U), z);
+    ybar_normals_x2<kTable, kRepLog>(T, philox_block(K, S0, U), philox_block(K, S1, U), z);
     // a block's normals summed pairwise, then one compensated add
     if (b == 0) {
       z0 = z[0];
@@ -47,7 +59,7 @@ __device__ __forceinline__ double2 dataset_ybar2(const PhiloxKeys& K, double lam
   }
   if (rem) {
     const PhiloxBlockPart U = philox_block_part(F, n_full);
-    normals_x2(philox_block(K, S0, U), philox_block(K, S1, U), z);
+    ybar_normals_x2<kTable, kRepLog>(T, philox_block(K, S0, U), philox_block(K, S1, U), z);
     if (n_full == 0) {
       z0 = z[0];
     } else {
