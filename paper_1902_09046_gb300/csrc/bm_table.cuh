@@ -32,7 +32,9 @@
 // interleaved entry by entry, 32 KB), where lane l reads copy l % 16: the 16
 // lanes of a half-warp then hit 16 different bank pairs whatever their
 // entries, and a 64-bit table read costs the minimum two wavefronts instead
-// of about four and a half at random.  Both forms hold the same values.
+// of about four and a half at random.  Kernels with short-lived CTAs read
+// the compact layout from global memory instead (bm_tab_global).  All forms
+// hold the same values.
 #pragma once
 
 #include <stdint.h>
@@ -61,12 +63,11 @@ struct BmTab {
 // bytes) with all threads of the CTA; the caller synchronises before use.
 template <bool kRepLog>
 __device__ __forceinline__ void bm_load(unsigned char* smem) {
-  const uint4* hi = reinterpret_cast<const uint4*>(kBmScHiBits);
-  const uint4* lo = reinterpret_cast<const uint4*>(kBmScLoBits);
+  const uint4* sc = reinterpret_cast<const uint4*>(kBmTablesBits);
   uint4* d = reinterpret_cast<uint4*>(smem);
-  constexpr int nhi = kBmScHi / 2, nlo = kBmScLo / 2;  // two float2 per uint4
-  for (int t = threadIdx.x; t < nhi + nlo; t += blockDim.x) d[t] = t < nhi ? hi[t] : lo[t - nhi];
-  const uint2* lg = reinterpret_cast<const uint2*>(kBmLogBits);
+  constexpr int nsc = (kBmScHi + kBmScLo) / 2;  // two float2 per uint4
+  for (int t = threadIdx.x; t < nsc; t += blockDim.x) d[t] = sc[t];
+  const uint2* lg = reinterpret_cast<const uint2*>(kBmTablesBits) + kBmScHi + kBmScLo;
   uint2* dl = reinterpret_cast<uint2*>(smem + kBmScBytes);
   if (kRepLog) {
     for (int t = threadIdx.x; t < kBmLogBuckets * 16; t += blockDim.x) dl[t] = lg[t >> 4];
@@ -80,6 +81,17 @@ __device__ __forceinline__ BmTab bm_tab(const unsigned char* smem) {
   BmTab T;
   T.base = smem;
   T.lane8 = kRepLog ? 8u * (threadIdx.x & 15u) : 0u;
+  return T;
+}
+
+// The same tables read where the library keeps them in global memory (the
+// compact layout, cached in L1): for kernels whose CTAs live too briefly, or
+// are too small, to pay for a copy into shared memory.  Same values, so the
+// same results bit for bit.
+__device__ __forceinline__ BmTab bm_tab_global() {
+  BmTab T;
+  T.base = reinterpret_cast<const unsigned char*>(kBmTablesBits);
+  T.lane8 = 0u;
   return T;
 }
 

@@ -77,16 +77,12 @@ __global__ void __launch_bounds__(kEmThreads, 2) em_ou_fused_x2(const __grid_con
 constexpr int kPipeProducers = 6;
 constexpr int kPipeRound = 12;
 constexpr int kPipeThreads = 32 * (1 + kPipeProducers);
-constexpr size_t kPipeRingBytes = 2 * kPipeRound * 32 * sizeof(float4);
-constexpr size_t kPipeSmem = kPipeRingBytes + bm_smem_bytes<false>();
-
+// A CTA lives for one short pass over its 32 samples, so the producers read
+// the Box-Muller tables from global memory (L1-cached; bm_tab_global) rather
+// than copying 50 KB into shared memory per CTA.
 __global__ void __launch_bounds__(kPipeThreads) em_ou_pipe(const __grid_constant__ OUConst P, uint32_t base,
                                                            uint32_t n, double* __restrict__ dist_out) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  float4 (*ring)[kPipeRound][32] = reinterpret_cast<float4 (*)[kPipeRound][32]>(smem);
-  unsigned char* tabs = smem + kPipeRingBytes;
-  bm_load<false>(tabs);
-  __syncthreads();
+  __shared__ float4 ring[2][kPipeRound][32];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t i = blockIdx.x * 32 + lane;
   const bool valid = i < n;
@@ -98,7 +94,7 @@ __global__ void __launch_bounds__(kPipeThreads) em_ou_pipe(const __grid_constant
   const uint32_t n_blocks = (P.s_obs[n_obs - 1] + 3u) >> 2;  // blocks up to the last observation
   const uint32_t rounds = (n_blocks + kPipeRound - 1) / kPipeRound;
   if (warp > 0) {
-    const BmTab T = bm_tab<false>(tabs);
+    const BmTab T = bm_tab_global();
     const PhiloxFamily fam = philox_family(P.keys, kTagPath, P.sub);
     const PhiloxStream stream = philox_stream(P.keys, fam, g);
     for (uint32_t r = 0; r <= rounds; ++r) {
@@ -194,8 +190,6 @@ cudaError_t em_prepare() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(em_ou_fused<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(em_ou_fused<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(em_ou_fused<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(em_ou_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kPipeSmem));
   if (e == cudaSuccess) e = bm_hooks_prepare();
   if (e == cudaSuccess && bit) ready.fetch_or(bit, std::memory_order_acq_rel);
   return e;
@@ -207,7 +201,7 @@ cudaError_t launch_em_ou(const OUConst& P, uint64_t base, uint32_t n, float* the
   cudaError_t e = em_prepare();
   if (e != cudaSuccess) return e;
   if (!theta_out && !summ_out && n <= kPipeMaxN) {
-    em_ou_pipe<<<(n + 31) / 32, kPipeThreads, kPipeSmem, s>>>(P, static_cast<uint32_t>(base), n, dist_out);
+    em_ou_pipe<<<(n + 31) / 32, kPipeThreads, 0, s>>>(P, static_cast<uint32_t>(base), n, dist_out);
     return cudaGetLastError();
   }
   if (!theta_out && !summ_out) {

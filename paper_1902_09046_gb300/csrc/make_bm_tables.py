@@ -183,10 +183,10 @@ def write_header(cs, As, hi, lo):
     lines = [
         "// bm_tables.h -- written by make_bm_tables.py; do not edit.",
         "//",
-        "// binary32 bit patterns of the table-driven Box-Muller (rng.cuh):",
-        "//   kBmLogBits[2j..2j+1]  = (c_j, A_j = 2 ln c_j), j = 0..255, buckets of f in [3/4, 3/2);",
-        "//   kBmScHiBits[2i..2i+1] = (cos, sin)(2 pi i / 4096);",
-        "//   kBmScLoBits[2k..2k+1] = (cos b_k - 1, sin b_k), b_k = 2 pi (k + 1/2) 2^-23.",
+        "// binary32 bit patterns of the table-driven Box-Muller (bm_table.cuh), as float2 entries:",
+        "//   entries 0..4095     (cos, sin)(2 pi i / 4096);",
+        "//   entries 4096..6143  (cos b_k - 1, sin b_k), b_k = 2 pi (k + 1/2) 2^-23;",
+        "//   entries 6144..6399  (c_j, A_j = 2 ln c_j), j = 0..255, buckets of f in [3/4, 3/2).",
         "#pragma once",
         "",
         "#include <stdint.h>",
@@ -199,13 +199,13 @@ def write_header(cs, As, hi, lo):
         f"constexpr uint32_t kBmLogK = 0x{int(np.float32(K_HI).view(np.uint32)):08x}u;  // RN(-2 ln 2)",
         "",
     ]
-    for name, arr in (("kBmLogBits", np.stack([cs, As], 1)), ("kBmScHiBits", hi), ("kBmScLoBits", lo)):
-        flat = np.asarray(arr, np.float32).ravel()
-        lines.append(f"__device__ const __align__(16) uint32_t {name}[{flat.size}] = {{")
-        for r0 in range(0, flat.size, 8):
-            lines.append("    " + _hex(flat[r0:r0 + 8]) + ",")
-        lines.append("};")
-        lines.append("")
+    flat = np.concatenate([np.asarray(a, np.float32).ravel() for a in (hi, lo, np.stack([cs, As], 1))])
+    lines.append("// One array in the compact layout: the sin/cos tables, then the log table.")
+    lines.append(f"__device__ const __align__(16) uint32_t kBmTablesBits[{flat.size}] = {{")
+    for r0 in range(0, flat.size, 8):
+        lines.append("    " + _hex(flat[r0:r0 + 8]) + ",")
+    lines.append("};")
+    lines.append("")
     lines.append("}  // namespace ppabc")
     with open(OUT, "w") as f:
         f.write("\n".join(lines) + "\n")
