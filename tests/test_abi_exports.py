@@ -95,3 +95,54 @@ def test_no_device_is_reported_as_error_not_fallback(lib):
     b = binding.load_library()
     rc = b.ppabc_device_check()
     assert rc in (binding.PPABC_ECUDA, binding.PPABC_ENODEV)
+
+
+def test_merge_entry_points_validate_before_any_launch(lib):
+    """abc_select_candidates / abc_merge_candidates (the exchange step of a
+    sample-sharded job) reject every malformed call on the host, before the
+    device is touched; the pointers below are aligned dummies that the calls
+    never dereference."""
+    b = binding.load_library()
+    P = ctypes.c_void_p
+    a = P(1 << 12)
+    EINVAL, ENOMEM = binding.PPABC_EINVAL, binding.PPABC_ENOMEM
+    cand = b.abc_select_candidates
+    assert cand(None, 10, 0, None, None, 0, None, None, None, None) == binding.PPABC_OK  # nothing to record
+    assert cand(a, 4, 0, a, a, 5, a, a, a, None) == EINVAL  # more candidates than samples
+    assert b"count" in b.ppabc_last_error()
+    assert cand(a, 1 << 32, 0, a, a, 5, a, a, a, None) == EINVAL  # n must fit 32 bits
+    assert cand(None, 10, 0, a, a, 5, a, a, a, None) == EINVAL  # NULL distances
+    assert cand(a, 10, 0, a, a, 5, a, None, a, None) == EINVAL  # NULL index output
+    assert cand(a, 10, 0, a, P((1 << 12) + 8), 5, a, a, a, None) == EINVAL  # records not 16-byte aligned
+    assert cand(a, 10, (1 << 32) - 5, a, a, 5, a, a, a, None) == EINVAL  # global indices past 2^32
+    assert b"sample_base" in b.ppabc_last_error()
+
+    ws = b.abc_merge_workspace_bytes
+    assert ws(1, 1) > 0 and ws(1000, 10) % 256 == 0
+    assert ws(1 << 20, 100) > ws(1000, 100) and ws(1000, 900) >= ws(1000, 10)
+    need = ws(100, 10)
+    merge = b.abc_merge_candidates
+    wsp = P(1 << 16)
+    assert merge(a, a, a, 100, 0, a, a, a, None, None, wsp, need, None) == EINVAL  # k = 0
+    assert merge(a, a, a, 100, 101, a, a, a, None, None, wsp, need, None) == EINVAL  # k > m
+    assert b"k must be" in b.ppabc_last_error()
+    assert merge(a, a, a, 1 << 32, 10, a, a, a, None, None, wsp, need, None) == EINVAL  # m must fit 32 bits
+    assert merge(a, None, a, 100, 10, a, a, a, None, None, wsp, need, None) == EINVAL  # NULL global indices
+    assert merge(a, a, a, 100, 10, a, a, None, None, None, wsp, need, None) == EINVAL  # NULL count output
+    assert merge(a, a, a, 100, 10, a, P((1 << 12) + 4), a, None, None, wsp, need, None) == EINVAL  # rec_out
+    assert merge(a, a, a, 100, 10, a, a, a, None, None, wsp, need - 1, None) == ENOMEM  # workspace too small
+    assert merge(a, a, a, 100, 10, a, a, a, None, None, None, need, None) == ENOMEM  # no workspace
+    assert merge(a, a, a, 100, 10, a, a, a, None, None, P((1 << 16) + 128), need, None) == EINVAL  # alignment
+    assert b"256-byte" in b.ppabc_last_error()
+
+
+def test_device_info_without_gpu(lib):
+    import torch
+    b = binding.load_library()
+    assert b.ppabc_device_info(None, None) == binding.PPABC_EINVAL
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    sm, clk = ctypes.c_int(-1), ctypes.c_int(-1)
+    assert b.ppabc_device_info(ctypes.byref(sm), ctypes.byref(clk)) in (binding.PPABC_ECUDA, binding.PPABC_ENODEV)
+    with pytest.raises(RuntimeError):
+        binding.device_info()
