@@ -244,7 +244,7 @@ def kernel_source_hash():
 
 
 def profiled_traffic(n_samples):
-    """DRAM bytes per em_ou_fused launch from the committed ncu summary, scaled
+    """DRAM bytes per em_ou_fused_x2 launch from the committed ncu summary, scaled
     to this launch size; None if absent or the kernel changed since."""
     path = os.path.join(ROOT, "profiles", "em_ou_fused_traffic.json")
     try:
@@ -420,7 +420,7 @@ def gpu_arm(args):
         e2e_s = float(t.item())
     e2e_value = units / e2e_s
 
-    # Roofline of the dominant kernel (em_ou_fused): 2 MUFU-class operations
+    # Roofline of the dominant kernel (em_ou_fused_x2): 2 MUFU-class operations
     # (log, sqrt, sin, cos per Box-Muller pair) per path-step against 16 MUFU
     # lanes per SM per clock on the device's SMs at its maximum SM clock.
     em_avg_s = statistics.mean(em_ms) / 1e3

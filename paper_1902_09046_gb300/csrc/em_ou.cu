@@ -1,50 +1,37 @@
-// em_ou.cu -- fused prior-predictive OU kernel and the raw RNG kernels.
+// em_ou.cu -- fused prior-predictive OU kernels and the raw RNG kernels.
 //
-// em_ou_fused: one sample path per thread.  Prior draw, Euler-Maruyama path,
-// summaries and discrepancy all happen in registers; the only global traffic
-// is the optional theta / summary write and one binary64 distance per sample.
-// This replaces the paper's block-of-VECL SIMD loop with pre-generated
-// normals (Sec. 3.4): on the GPU a warp is the SIMD vector, the sample index
-// is the lane, and the normals never touch memory.
+// Prior draw, Euler-Maruyama path, summaries and discrepancy all happen in
+// registers; the only global traffic is the optional theta / summary write
+// and one binary64 distance per sample.  This replaces the paper's
+// block-of-VECL SIMD loop with pre-generated normals (Sec. 3.4): on the GPU a
+// warp is the SIMD vector, the sample index is the lane, and the normals
+// never touch memory.  Two kernels, chosen by the launch size, give the same
+// results bit for bit:
+//   em_ou_fused_x2: two interleaved paths per thread (ou_path2), for large
+//     launches;
+//   em_ou_pipe: a warp-specialised pipeline over 32 samples per CTA, for
+//     small ones.
+// Both write theta ([3][n]) and the summaries ([n_obs][n]) when asked.
 #include <atomic>
 
 #include "internal.h"
 
 namespace ppabc {
 
-// The path kernels keep the Box-Muller tables in shared memory (80 KB with
-// the lane-replicated log table): 512-thread CTAs, two per SM, 32 warps.
+// The two-path kernel keeps the Box-Muller tables in shared memory (80 KB
+// with the lane-replicated log table): 512-thread CTAs, two per SM, 32 warps.
 constexpr int kEmThreads = 512;
 constexpr size_t kEmSmem = bm_smem_bytes<true>();
 
+// Samples i and i + kEmThreads of each CTA's 2 kEmThreads range, interleaved
+// (ou_path2).  Past the end of the launch the second path repeats the first
+// (same index, so the same values) and writes nothing of its own: its
+// summary row pointer is the first path's.
 template <bool kWantTheta, bool kWantSumm>
-__global__ void __launch_bounds__(kEmThreads, 2) em_ou_fused(const __grid_constant__ OUConst P,
-                                                             uint32_t base, uint32_t n,
-                                                             float* __restrict__ theta_out,
-                                                             double* __restrict__ summ_out,
-                                                             double* __restrict__ dist_out) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  bm_load<true>(smem);
-  __syncthreads();
-  const BmTab T = bm_tab<true>(smem);
-  const uint32_t i = blockIdx.x * kEmThreads + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t g = base + i;
-  float th1, th2, th3;
-  ou_prior(P, g, th1, th2, th3);
-  if (kWantTheta) {
-    theta_out[i] = th1;
-    theta_out[static_cast<size_t>(n) + i] = th2;
-    theta_out[2 * static_cast<size_t>(n) + i] = th3;
-  }
-  dist_out[i] = ou_path<kWantSumm, true>(P, T, g, th1, th2, th3, kWantSumm ? summ_out + i : nullptr, n);
-}
-
-// Two samples per thread (samples i and i + kEmThreads of each CTA's
-// 2 kEmThreads range), interleaved; see ou_path2.  Used when neither theta
-// nor the summaries are requested (the benchmark and batch paths).
 __global__ void __launch_bounds__(kEmThreads, 2) em_ou_fused_x2(const __grid_constant__ OUConst P,
                                                                 uint32_t base, uint32_t n,
+                                                                float* __restrict__ theta_out,
+                                                                double* __restrict__ summ_out,
                                                                 double* __restrict__ dist_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   bm_load<true>(smem);
@@ -53,14 +40,26 @@ __global__ void __launch_bounds__(kEmThreads, 2) em_ou_fused_x2(const __grid_con
   const uint32_t i0 = blockIdx.x * (2 * kEmThreads) + threadIdx.x;
   const uint32_t i1 = i0 + kEmThreads;
   if (i0 >= n) return;
-  const uint32_t gi[2] = {base + i0, base + (i1 < n ? i1 : i0)};
+  const bool has1 = i1 < n;
+  const uint32_t gi[2] = {base + i0, base + (has1 ? i1 : i0)};
   float th1[2], th2[2], th3[2];
   ou_prior(P, gi[0], th1[0], th2[0], th3[0]);
   ou_prior(P, gi[1], th1[1], th2[1], th3[1]);
+  if (kWantTheta) {
+    theta_out[i0] = th1[0];
+    theta_out[static_cast<size_t>(n) + i0] = th2[0];
+    theta_out[2 * static_cast<size_t>(n) + i0] = th3[0];
+    if (has1) {
+      theta_out[i1] = th1[1];
+      theta_out[static_cast<size_t>(n) + i1] = th2[1];
+      theta_out[2 * static_cast<size_t>(n) + i1] = th3[1];
+    }
+  }
   double d[2];
-  ou_path2<false, true>(P, T, gi, th1, th2, th3, nullptr, nullptr, 0, d);
+  ou_path2<kWantSumm, true>(P, T, gi, th1, th2, th3, kWantSumm ? summ_out + i0 : nullptr,
+                            kWantSumm ? summ_out + (has1 ? i1 : i0) : nullptr, n, d);
   dist_out[i0] = d[0];
-  if (i1 < n) dist_out[i1] = d[1];
+  if (has1) dist_out[i1] = d[1];
 }
 
 // Small launches (n up to kPipeMaxN samples): a warp-specialised pipeline.
@@ -80,8 +79,11 @@ constexpr int kPipeThreads = 32 * (1 + kPipeProducers);
 // A CTA lives for one short pass over its 32 samples, so the producers read
 // the Box-Muller tables from global memory (L1-cached; bm_tab_global) rather
 // than copying 50 KB into shared memory per CTA.
+template <bool kWantTheta, bool kWantSumm>
 __global__ void __launch_bounds__(kPipeThreads) em_ou_pipe(const __grid_constant__ OUConst P, uint32_t base,
-                                                           uint32_t n, double* __restrict__ dist_out) {
+                                                           uint32_t n, float* __restrict__ theta_out,
+                                                           double* __restrict__ summ_out,
+                                                           double* __restrict__ dist_out) {
   __shared__ float4 ring[2][kPipeRound][32];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t i = blockIdx.x * 32 + lane;
@@ -110,6 +112,11 @@ __global__ void __launch_bounds__(kPipeThreads) em_ou_pipe(const __grid_constant
     return;
   }
   // Warp 0: ou_path's walk, one counter block at a time.
+  if (kWantTheta && valid) {
+    theta_out[i] = th1;
+    theta_out[static_cast<size_t>(n) + i] = th2;
+    theta_out[2 * static_cast<size_t>(n) + i] = th3;
+  }
   const float k = th1 * P.dt;
   float Y = P.x0 - th2;
   float comp;
@@ -160,6 +167,7 @@ __global__ void __launch_bounds__(kPipeThreads) em_ou_pipe(const __grid_constant
               const double x = th2d + (static_cast<double>(Y) - static_cast<double>(comp));
               const double rr = x - P.y[j];
               acc = fma(rr, rr, acc);
+              if (kWantSumm && valid) summ_out[static_cast<size_t>(j) * n + i] = x;
               ++j;
               s_next = (j < n_obs) ? P.s_obs[j] : 0xFFFFFFFFu;
             }
@@ -185,41 +193,46 @@ cudaError_t em_prepare() {
   const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
   if (bit && (ready.load(std::memory_order_acquire) & bit)) return cudaSuccess;
   const int big = static_cast<int>(kEmSmem);
-  e = cudaFuncSetAttribute(em_ou_fused_x2, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(em_ou_fused<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(em_ou_fused<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(em_ou_fused<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(em_ou_fused<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  e = cudaFuncSetAttribute(em_ou_fused_x2<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(em_ou_fused_x2<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(em_ou_fused_x2<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(em_ou_fused_x2<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = bm_hooks_prepare();
   if (e == cudaSuccess && bit) ready.fetch_or(bit, std::memory_order_acq_rel);
   return e;
 }
+
+namespace {
+
+template <bool kWantTheta, bool kWantSumm>
+cudaError_t launch_em_ou_as(const OUConst& P, uint32_t base, uint32_t n, float* theta_out, double* summ_out,
+                            double* dist_out, cudaStream_t s) {
+  if (n <= kPipeMaxN) {
+    em_ou_pipe<kWantTheta, kWantSumm><<<(n + 31) / 32, kPipeThreads, 0, s>>>(P, base, n, theta_out, summ_out,
+                                                                             dist_out);
+  } else {
+    const dim3 grid((n + 2 * kEmThreads - 1) / (2 * kEmThreads));
+    em_ou_fused_x2<kWantTheta, kWantSumm><<<grid, kEmThreads, kEmSmem, s>>>(P, base, n, theta_out, summ_out,
+                                                                            dist_out);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
 
 cudaError_t launch_em_ou(const OUConst& P, uint64_t base, uint32_t n, float* theta_out,
                          double* summ_out, double* dist_out, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   cudaError_t e = em_prepare();
   if (e != cudaSuccess) return e;
-  if (!theta_out && !summ_out && n <= kPipeMaxN) {
-    em_ou_pipe<<<(n + 31) / 32, kPipeThreads, 0, s>>>(P, static_cast<uint32_t>(base), n, dist_out);
-    return cudaGetLastError();
-  }
-  if (!theta_out && !summ_out) {
-    const dim3 grid2((n + 2 * kEmThreads - 1) / (2 * kEmThreads));
-    em_ou_fused_x2<<<grid2, kEmThreads, kEmSmem, s>>>(P, static_cast<uint32_t>(base), n, dist_out);
-    return cudaGetLastError();
-  }
-  const dim3 grid((n + kEmThreads - 1) / kEmThreads);
   const uint32_t b = static_cast<uint32_t>(base);
-  if (theta_out && summ_out)
-    em_ou_fused<true, true><<<grid, kEmThreads, kEmSmem, s>>>(P, b, n, theta_out, summ_out, dist_out);
-  else if (theta_out)
-    em_ou_fused<true, false><<<grid, kEmThreads, kEmSmem, s>>>(P, b, n, theta_out, summ_out, dist_out);
-  else if (summ_out)
-    em_ou_fused<false, true><<<grid, kEmThreads, kEmSmem, s>>>(P, b, n, theta_out, summ_out, dist_out);
-  else
-    em_ou_fused<false, false><<<grid, kEmThreads, kEmSmem, s>>>(P, b, n, theta_out, summ_out, dist_out);
-  return cudaGetLastError();
+  if (theta_out && summ_out) return launch_em_ou_as<true, true>(P, b, n, theta_out, summ_out, dist_out, s);
+  if (theta_out) return launch_em_ou_as<true, false>(P, b, n, theta_out, summ_out, dist_out, s);
+  if (summ_out) return launch_em_ou_as<false, true>(P, b, n, theta_out, summ_out, dist_out, s);
+  return launch_em_ou_as<false, false>(P, b, n, theta_out, summ_out, dist_out, s);
 }
 
 // ---------------------------------------------------------------------------

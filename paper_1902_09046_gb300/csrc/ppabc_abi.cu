@@ -172,7 +172,7 @@ int abc_prior_predictive(const ppabc_ou_model* h_model, const double* h_y_obs, u
   if (rc) return rc;
   return check_cuda(launch_em_ou(P, sample_base, static_cast<uint32_t>(n_samples), theta_out, summ_out,
                                  dist_out, static_cast<cudaStream_t>(stream)),
-                    "em_ou_fused launch");
+                    "prior-predictive launch");
 }
 
 size_t abc_select_workspace_bytes(uint64_t n) { return select_workspace_bytes(n); }

@@ -90,8 +90,11 @@ def test_small_workload_parity_and_accept_set():
                                                       (1000, 1, 1, 0.3, 10.0),
                                                       (4, 4, 129, -1.0, 0.4),
                                                       (250, 32, 1000, 2.0, 10.0),
-                                                      (101, 7, 4099, 0.0, 10.0)])
+                                                      (101, 7, 4099, 0.0, 10.0),
+                                                      (40, 10, 50001, 0.0, 10.0)])
 def test_ragged_models(n_steps, n_obs, n, x0, t_end):
+    """n <= 49152 runs the pipelined kernel, n = 50001 the two-path kernel
+    (with a ragged last CTA), both writing theta and the summaries."""
     model = workloads.ou_model(n_steps, t_end=t_end, n_obs=n_obs, x0=x0)
     y = np.linspace(-0.5, 1.0, n_obs)
     compare_paths(model, y, n, seed=11, sub=2)
@@ -112,33 +115,41 @@ def test_fixed_theta_and_sample_base_sharding():
 
 
 @pytest.mark.parametrize("n", [1, 255, 256, 257, 100_001])
-def test_two_paths_per_thread_is_bit_identical(n):
-    """Without theta or summary outputs the kernel runs two interleaved paths
-    per thread; every distance equals the one-path-per-thread kernel's."""
+def test_theta_and_summary_outputs_leave_the_distances_unchanged(n):
     binding = require_gpu()
     w = workloads.abc_small()
     a = binding.abc_prior_predictive(w.model, w.y_obs, n, w.seed, sample_base=77, want_theta=False)
     b = binding.abc_prior_predictive(w.model, w.y_obs, n, w.seed, sample_base=77, want_theta=True)
+    c = binding.abc_prior_predictive(w.model, w.y_obs, n, w.seed, sample_base=77, want_theta=True,
+                                     want_summ=True)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(to_np(a["dist"]), to_np(b["dist"]))
+    np.testing.assert_array_equal(to_np(a["dist"]), to_np(c["dist"]))
+    np.testing.assert_array_equal(to_np(b["theta"]), to_np(c["theta"]))
 
 
 @pytest.mark.parametrize("n_steps,n_obs,n", [(37, 10, 33), (1000, 1, 1), (4, 4, 129), (250, 32, 1000),
                                              (101, 7, 4099), (7, 7, 65), (9, 3, 31), (1000, 10, 49152),
                                              (1000, 10, 49153)])
 def test_small_launch_pipeline_is_bit_identical(n_steps, n_obs, n):
-    """Small launches without theta or summaries run the warp-specialised
-    pipeline (normals drawn by producer warps, paths walked by one warp);
-    every distance equals the one-path-per-thread kernel's, for step counts
-    that are not multiples of four and for several observations in one
-    counter block."""
+    """Launches of up to 49152 samples run the warp-specialised pipeline
+    (normals drawn by producer warps, paths walked by one warp), larger ones
+    two interleaved paths per thread.  The same samples (same base) from a
+    launch of each kind: distances, theta and summaries are equal bit for bit,
+    for step counts that are not multiples of four and for several
+    observations in one counter block."""
     binding = require_gpu()
     model = workloads.ou_model(n_steps, t_end=0.01 * n_steps, n_obs=n_obs)
     y = np.linspace(-0.5, 1.0, n_obs)
-    a = binding.abc_prior_predictive(model, y, n, 11, sample_base=5, want_theta=False)
-    b = binding.abc_prior_predictive(model, y, n, 11, sample_base=5, want_theta=True)
-    torch.cuda.synchronize()
-    np.testing.assert_array_equal(to_np(a["dist"]), to_np(b["dist"]))
+    big = max(n, 49153)
+    for kw in ({"want_theta": False}, {"want_theta": True, "want_summ": True}):
+        a = binding.abc_prior_predictive(model, y, n, 11, sample_base=5, **kw)
+        b = binding.abc_prior_predictive(model, y, big, 11, sample_base=5, **kw)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(to_np(a["dist"]), to_np(b["dist"])[:n])
+        if kw["want_theta"]:
+            np.testing.assert_array_equal(to_np(a["theta"]), to_np(b["theta"])[:, :n])
+            np.testing.assert_array_equal(to_np(a["summ"]), to_np(b["summ"])[:, :n])
 
 
 def test_empty_and_invalid():
