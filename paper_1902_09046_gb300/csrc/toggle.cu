@@ -133,6 +133,9 @@ __global__ void __launch_bounds__(kTgThreads) toggle_abc(const __grid_constant__
     uint32_t b = 0;
     uint32_t j = 0;
     float2 z[4];
+    // Unrolled by 4 (paper-size benchmark 100.7 -> 97.3 ms; the same
+    // operations in the same order).
+#pragma unroll 4
     for (; j + 2 <= steps; j += 2, ++b) {
       const PhiloxBlockPart Ub = philox_block_part(fam, b);
       normals_x2(philox_block(P.keys, S0, Ub), philox_block(P.keys, S1, Ub), z);
