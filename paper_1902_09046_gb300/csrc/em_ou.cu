@@ -74,8 +74,9 @@ __global__ void __launch_bounds__(kEmThreads, 2) em_ou_fused_x2(const __grid_con
 // same values as the replicated one).  Rounds end at a CTA barrier; nothing
 // spins.
 constexpr int kPipeProducers = 6;
-constexpr int kPipeRound = 12;
+constexpr int kPipeRound = 24;
 constexpr int kPipeThreads = 32 * (1 + kPipeProducers);
+static_assert(kPipeRound % kPipeProducers == 0, "every producer draws the same number of blocks a round");
 // A CTA lives for one short pass over its 32 samples, so the producers read
 // the Box-Muller tables from global memory (L1-cached; bm_tab_global) rather
 // than copying 50 KB into shared memory per CTA.
@@ -101,7 +102,11 @@ __global__ void __launch_bounds__(kPipeThreads) em_ou_pipe(const __grid_constant
     const PhiloxStream stream = philox_stream(P.keys, fam, g);
     for (uint32_t r = 0; r <= rounds; ++r) {
       if (r < rounds) {
-        for (uint32_t q = warp - 1; q < static_cast<uint32_t>(kPipeRound); q += kPipeProducers) {
+        // Blocks q = warp - 1 + kPipeProducers h of the round: a fixed count,
+        // so the two chains interleave (5% faster at N = 10^4).
+#pragma unroll
+        for (uint32_t h = 0; h < static_cast<uint32_t>(kPipeRound / kPipeProducers); ++h) {
+          const uint32_t q = warp - 1 + h * kPipeProducers;
           const uint32_t b = r * kPipeRound + q;
           if (b < n_blocks)
             ring[r & 1u][q][lane] = scaled_tnormals_of<false>(T, philox_block(P.keys, fam, stream, b), c);
@@ -134,9 +139,33 @@ __global__ void __launch_bounds__(kPipeThreads) em_ou_pipe(const __grid_constant
   float4 zp = make_float4(0.f, 0.f, 0.f, 0.f);
   for (uint32_t r = 0; r <= rounds; ++r) {
     if (r > 0) {
-      for (uint32_t q = 0; q < static_cast<uint32_t>(kPipeRound) && j < n_obs; ++q) {
-        if ((r - 1) * kPipeRound + q >= n_blocks) break;
-        const float4 z = ring[(r - 1) & 1u][q][lane];
+      const float4(&rd)[kPipeRound][32] = ring[(r - 1) & 1u];
+      const uint32_t done = (r - 1) * kPipeRound;  // < n_blocks
+      const uint32_t qend = n_blocks - done < static_cast<uint32_t>(kPipeRound) ? n_blocks - done
+                                                                                : static_cast<uint32_t>(kPipeRound);
+      uint32_t q = 0;
+      while (q < qend && j < n_obs) {
+        // Four whole blocks of the current run: the pair updates that the
+        // block-at-a-time code below makes, in the same order, with the four
+        // ring reads issued first.  Without a pending block the pairs are
+        // (b, b+1), (b+2, b+3); with one, (zp, b), (b+1, b+2), and b+3 becomes
+        // the pending block, which needs a block after it in the run.
+        if (!seg && q + 4 <= qend && (pending ? b + 4 < b_end : b + 4 <= b_end)) {
+          const float4 z0 = rd[q][lane], z1 = rd[q + 1][lane], z2 = rd[q + 2][lane], z3 = rd[q + 3][lane];
+          if (pending) {
+            em_block8(Y, comp, E4, zp, z0);
+            em_block8(Y, comp, E4, z1, z2);
+            zp = z3;
+          } else {
+            em_block8(Y, comp, E4, z0, z1);
+            em_block8(Y, comp, E4, z2, z3);
+          }
+          b += 4;
+          q += 4;
+          continue;
+        }
+        const float4 z = rd[q][lane];
+        ++q;
         if (seg) {
           s_next = P.s_obs[j];
           b_end = b + (s_next > s + 4u ? (s_next - s - 1u) >> 2 : 0u);
@@ -181,7 +210,7 @@ __global__ void __launch_bounds__(kPipeThreads) em_ou_pipe(const __grid_constant
   if (valid) dist_out[i] = sqrt(acc);
 }
 
-constexpr uint32_t kPipeMaxN = 49152;  // above about this the two-path kernel is faster
+constexpr uint32_t kPipeMaxN = 98304;  // above about this the two-path kernel is faster
 
 cudaError_t bm_hooks_prepare();
 

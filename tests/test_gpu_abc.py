@@ -91,9 +91,9 @@ def test_small_workload_parity_and_accept_set():
                                                       (4, 4, 129, -1.0, 0.4),
                                                       (250, 32, 1000, 2.0, 10.0),
                                                       (101, 7, 4099, 0.0, 10.0),
-                                                      (40, 10, 50001, 0.0, 10.0)])
+                                                      (40, 10, 100001, 0.0, 10.0)])
 def test_ragged_models(n_steps, n_obs, n, x0, t_end):
-    """n <= 49152 runs the pipelined kernel, n = 50001 the two-path kernel
+    """n <= 98304 runs the pipelined kernel, n = 100001 the two-path kernel
     (with a ragged last CTA), both writing theta and the summaries."""
     model = workloads.ou_model(n_steps, t_end=t_end, n_obs=n_obs, x0=x0)
     y = np.linspace(-0.5, 1.0, n_obs)
@@ -129,10 +129,10 @@ def test_theta_and_summary_outputs_leave_the_distances_unchanged(n):
 
 
 @pytest.mark.parametrize("n_steps,n_obs,n", [(37, 10, 33), (1000, 1, 1), (4, 4, 129), (250, 32, 1000),
-                                             (101, 7, 4099), (7, 7, 65), (9, 3, 31), (1000, 10, 49152),
-                                             (1000, 10, 49153)])
+                                             (101, 7, 4099), (7, 7, 65), (9, 3, 31), (1000, 10, 98304),
+                                             (1000, 10, 98305)])
 def test_small_launch_pipeline_is_bit_identical(n_steps, n_obs, n):
-    """Launches of up to 49152 samples run the warp-specialised pipeline
+    """Launches of up to 98304 samples run the warp-specialised pipeline
     (normals drawn by producer warps, paths walked by one warp), larger ones
     two interleaved paths per thread.  The same samples (same base) from a
     launch of each kind: distances, theta and summaries are equal bit for bit,
@@ -141,7 +141,7 @@ def test_small_launch_pipeline_is_bit_identical(n_steps, n_obs, n):
     binding = require_gpu()
     model = workloads.ou_model(n_steps, t_end=0.01 * n_steps, n_obs=n_obs)
     y = np.linspace(-0.5, 1.0, n_obs)
-    big = max(n, 49153)
+    big = max(n, 98305)
     for kw in ({"want_theta": False}, {"want_theta": True, "want_summ": True}):
         a = binding.abc_prior_predictive(model, y, n, 11, sample_base=5, **kw)
         b = binding.abc_prior_predictive(model, y, big, 11, sample_base=5, **kw)
