@@ -330,11 +330,18 @@ void scheduler(ppabc_server* S) {
     if (changed) S->done_cv.notify_all();
     bool any_busy = false;
     for (auto& sl : S->slots) any_busy |= sl.busy;
-    // Busy: poll completions often.  Idle: sleep until a submit wakes us.
-    if (any_busy)
-      S->cv.wait_for(lock, std::chrono::microseconds(20));
-    else
+    // Busy: poll the completion events about every 2 us, with the lock
+    // released meanwhile so that submits go through.  (A timed wait would
+    // sleep at least the thread's timer slack, about 50 us on Linux, and that
+    // would land in every job's latency.)  Idle: sleep until a submit wakes us.
+    if (any_busy) {
+      lock.unlock();
+      const auto t_spin = std::chrono::steady_clock::now();
+      while (std::chrono::steady_clock::now() - t_spin < std::chrono::microseconds(2)) std::this_thread::yield();
+      lock.lock();
+    } else {
       S->cv.wait_for(lock, std::chrono::milliseconds(50));
+    }
   }
 }
 
