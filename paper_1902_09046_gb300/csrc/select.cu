@@ -11,13 +11,16 @@
 // with Chan's pairwise update in a fixed order.
 //
 // Threshold mode (k = 0) skips the radix passes: the key of epsilon itself is
-// the cut.  Ties at the cut go to the smaller index in both modes.  Up to
-// 24576 distances one CTA does all of it from shared memory in a single
-// launch, for the many small jobs of a serving mix.
+// the cut.  Ties at the cut go to the smaller index in both modes.  For the
+// many small jobs of a serving mix, the whole selection runs in one launch
+// from shared memory: up to 12288 distances in one CTA, up to 196608 in a
+// thread-block cluster of eight CTAs that pool their shared memory.
 #include <math.h>
 #include <string.h>
 
 #include <atomic>
+
+#include <cooperative_groups.h>
 
 #include "dfloat.cuh"
 #include "internal.h"
@@ -524,11 +527,12 @@ __device__ __forceinline__ DF df_div_f(DF a, float b) {
 // binary64 divisions there did), and the trees are rolled loops: this one-CTA kernel runs each instruction
 // once, so its time follows its code size.  s_S1, s_S2, s_cw hold one value
 // per warp and dimension, s_nw one count per warp (kWarps <= 32).
+// cta_moment_sums is the part up to the CTA's totals (returns true in warp 0,
+// whose lanes then all hold them); store_moments the finish.
 template <int kWarps>
-__device__ __forceinline__ void finish_moments(DF (&S1)[3], DF (&S2)[3], const float (&cw)[3], unsigned int nw,
-                                               unsigned long long k, DF (*s_S1)[kWarps], DF (*s_S2)[kWarps],
-                                               float (*s_cw)[kWarps], const unsigned int* s_nw,
-                                               const float* s_c0, double* post_out) {
+__device__ __forceinline__ bool cta_moment_sums(DF (&S1)[3], DF (&S2)[3], const float (&cw)[3], unsigned int nw,
+                                                DF (*s_S1)[kWarps], DF (*s_S2)[kWarps], float (*s_cw)[kWarps],
+                                                const unsigned int* s_nw, const float* s_c0) {
   static_assert(kWarps <= 32, "one warp sums the warps' partial sums");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (nw != 0u) {  // warp-uniform: the sums of a warp without accepted samples are zero
@@ -550,7 +554,7 @@ __device__ __forceinline__ void finish_moments(DF (&S1)[3], DF (&S2)[3], const f
     }
   }
   __syncthreads();
-  if (warp != 0) return;
+  if (warp != 0) return false;
   const unsigned int n_w = lane < kWarps ? s_nw[lane] : 0u;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -571,6 +575,15 @@ __device__ __forceinline__ void finish_moments(DF (&S1)[3], DF (&S2)[3], const f
       S2[d] = df_add(S2[d], DF{__shfl_xor_sync(0xFFFFFFFFu, S2[d].hi, o), __shfl_xor_sync(0xFFFFFFFFu, S2[d].lo, o)});
     }
   }
+  return true;
+}
+
+// mean = c + S1 / k and the unbiased variance (S2 - S1 (S1 / k)) / (k - 1)
+// from the totals about the shift s_c0, written by lanes 0..2 (dimension =
+// lane).
+__device__ __forceinline__ void store_moments(const DF (&S1)[3], const DF (&S2)[3], unsigned long long k,
+                                              const float* s_c0, double* post_out) {
+  const int lane = threadIdx.x & 31;
   if (lane < 3 && post_out) {
     const DF a = lane == 0 ? S1[0] : (lane == 1 ? S1[1] : S1[2]);
     const DF b = lane == 0 ? S2[0] : (lane == 1 ? S2[1] : S2[2]);
@@ -579,6 +592,14 @@ __device__ __forceinline__ void finish_moments(DF (&S1)[3], DF (&S2)[3], const f
     post_out[lane] = k > 0 ? df_to_double(df_add_f(m, s_c0[lane])) : nan("");
     post_out[3 + lane] = k > 1 ? df_to_double(df_div_f(df_add(b, df_neg(df_mul(a, m))), kf - 1.0f)) : nan("");
   }
+}
+
+template <int kWarps>
+__device__ __forceinline__ void finish_moments(DF (&S1)[3], DF (&S2)[3], const float (&cw)[3], unsigned int nw,
+                                               unsigned long long k, DF (*s_S1)[kWarps], DF (*s_S2)[kWarps],
+                                               float (*s_cw)[kWarps], const unsigned int* s_nw,
+                                               const float* s_c0, double* post_out) {
+  if (cta_moment_sums<kWarps>(S1, S2, cw, nw, s_S1, s_S2, s_cw, s_nw, s_c0)) store_moments(S1, S2, k, s_c0, post_out);
 }
 
 // Adds (theta - c) and (theta - c)^2 to the double-float sums; each
@@ -859,6 +880,306 @@ __global__ void __launch_bounds__(kMidThreads, 1) select_mid(
   }
 }
 
+// ---------------------------------------------------------------------------
+// kMidMax < n <= kClusterMax distances: the same selection in one launch of a
+// thread-block cluster of kClusterCtas CTAs, which pools their shared memory.
+// CTA r holds the bit patterns of the index slice [lo, hi) (equal slices, a
+// multiple of 32 long, in index order).  A radix pass: every CTA builds the
+// histogram of its slice; CTA r sums bins [r kBinsPerCta, (r+1) kBinsPerCta)
+// over the cluster through distributed shared memory and posts their total
+// in CTA 0; the CTA whose bins hold the k-th key posts the digit there, and
+// every CTA reads it back.  The compaction runs per CTA as in select_mid,
+// with the keys equal to the cut and the accepted ones before each slice
+// counted from the CTAs' counts posted in CTA 0; the moments are summed per
+// CTA about the first accepted theta overall, then over the CTAs in rank
+// order.  Every thread takes part in every cluster barrier and none leaves
+// before the last one, after which no CTA touches another's shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kClusterCtas = 8;
+constexpr uint32_t kClusterMax = kClusterCtas * kMidMax;
+// Below about this many distances the one CTA is faster (no cluster
+// barriers): 14.4 against 15.8 us at n = 10^4, 19.0 against 16.2 us at 16384.
+constexpr uint32_t kOneCtaMax = 12288;
+constexpr int kBinsPerCta = kBins / kClusterCtas;
+static_assert(kBinsPerCta * kClusterCtas == kBins && kBinsPerCta <= kMidThreads, "bins split evenly over the CTAs");
+static_assert(kClusterCtas <= 32, "one lane per CTA");
+
+template <bool kTheta>
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kMidThreads, 1) select_cluster(
+    const double* __restrict__ dist, uint32_t n, unsigned long long k, bool threshold,
+    unsigned long long cut_thr, double eps_thr, const __grid_constant__ OUConst prm, uint32_t base,
+    const float* __restrict__ theta, uint32_t* __restrict__ idx_out, float4* __restrict__ rec_out,
+    unsigned long long cap, unsigned long long* __restrict__ n_acc_out, double* __restrict__ eps_out,
+    double* __restrict__ post_out) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const unsigned int rank = cluster.block_rank();
+  extern __shared__ unsigned long long s_raw[];  // this CTA's slice of bit patterns
+  __shared__ unsigned int h[kBins];
+  __shared__ unsigned int scan_smem[kMidWarps];
+  // CTA 0's copies of these are the cluster's: per-CTA counts, the digit
+  // found (prefix, mask, rank left, its bin's count), the cut's full key and
+  // the CTAs' moment sums.
+  __shared__ unsigned int c_tot[kClusterCtas], c_eq[kClusterCtas], c_acc[kClusterCtas];
+  __shared__ unsigned long long c_res[4];
+  __shared__ unsigned long long s_cut;
+  __shared__ DF c_S1[3 * kClusterCtas], c_S2[3 * kClusterCtas];
+  __shared__ unsigned int s_cnt[kClusterCtas];  // a local copy of one of the count arrays
+  __shared__ unsigned int acc_bits[kMidMax / 32];
+  __shared__ unsigned int s_weq[kMidWarps], s_wacc[kMidWarps];
+  __shared__ float s_shift[3];
+  __shared__ DF s_S1[3][kMidWarps], s_S2[3][kMidWarps];
+  __shared__ float s_cw[3][kMidWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned int lane_lt = (1u << lane) - 1u;
+  const uint32_t L = ((n + kClusterCtas - 1) / kClusterCtas + 31u) & ~31u;
+  const uint32_t lo = min(n, rank * L), hi = min(n, lo + L), m = hi - lo;
+  unsigned int* const tot0 = cluster.map_shared_rank(c_tot, 0);
+  unsigned int* const eq0 = cluster.map_shared_rank(c_eq, 0);
+  unsigned int* const acc0 = cluster.map_shared_rank(c_acc, 0);
+  unsigned long long* const res0 = cluster.map_shared_rank(c_res, 0);
+  // set here, before the first cluster barrier: the CTA that emits output
+  // position 0 writes every CTA's copy later
+  if (threadIdx.x < 3) s_shift[threadIdx.x] = 0.0f;
+  // 0. This CTA's slice into shared memory.
+  const unsigned long long* __restrict__ dbits = reinterpret_cast<const unsigned long long*>(dist) + lo;
+  for (uint32_t i0 = 0; i0 < m; i0 += kMidThreads * kMidChunk) {
+    unsigned long long t[kMidChunk];
+#pragma unroll
+    for (int j = 0; j < kMidChunk; ++j) {
+      const uint32_t i = i0 + j * kMidThreads + threadIdx.x;
+      t[j] = i < m ? __ldg(dbits + i) : 0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < kMidChunk; ++j) {
+      const uint32_t i = i0 + j * kMidThreads + threadIdx.x;
+      if (i < m) s_raw[i] = t[j];
+    }
+  }
+  __syncthreads();
+  unsigned long long prefix = 0ull, mask = 0ull, krem = k, bin_count = 0ull;
+  // 1. Radix select of the k-th smallest key over the cluster (skipped in
+  // threshold mode).
+  if (!threshold) {
+    for (int pass = 0; pass < kNumPasses; ++pass) {
+      const int shift = kPassShift[pass];
+      const unsigned long long dmask = (1ull << kPassBits[pass]) - 1ull;
+      for (int b = threadIdx.x; b < kBins; b += kMidThreads) h[b] = 0u;
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < m; i += kMidThreads) {
+        const unsigned long long key = key_of_bits(s_raw[i]);
+        if ((key & mask) == prefix) atomicAdd(&h[static_cast<unsigned int>((key >> shift) & dmask)], 1u);
+      }
+      cluster.sync();  // every CTA's histogram complete
+      unsigned int mine = 0;
+      if (threadIdx.x < kBinsPerCta) {
+        const unsigned int bin = rank * kBinsPerCta + threadIdx.x;
+#pragma unroll 1
+        for (int r = 0; r < kClusterCtas; ++r) mine += cluster.map_shared_rank(h, r)[bin];
+      }
+      unsigned int total;
+      const unsigned int before = block_exclusive_scan<unsigned int>(mine, &total, scan_smem);
+      if (threadIdx.x == 0) tot0[rank] = total;
+      cluster.sync();  // totals posted; no CTA reads another's histogram any more
+      if (threadIdx.x < kClusterCtas) s_cnt[threadIdx.x] = tot0[threadIdx.x];
+      __syncthreads();
+      if (threadIdx.x < kBinsPerCta) {
+        unsigned long long b0 = before;  // keys under the prefix in lower bins
+        for (unsigned int r = 0; r < rank; ++r) b0 += s_cnt[r];
+        if (b0 < krem && krem <= b0 + mine) {  // one thread in the cluster
+          res0[0] = prefix | (static_cast<unsigned long long>(rank * kBinsPerCta + threadIdx.x) << shift);
+          res0[1] = mask | (dmask << shift);
+          res0[2] = krem - b0;
+          res0[3] = mine;
+        }
+      }
+      cluster.sync();  // the digit posted
+      prefix = res0[0];
+      mask = res0[1];
+      krem = res0[2];
+      bin_count = res0[3];
+      if (bin_count == 1ull) break;  // cluster-uniform, as in select_mid
+    }
+  }
+  const unsigned long long cut = threshold ? cut_thr : prefix;
+  const unsigned long long cmask = threshold ? 0xFFFFFFFFFFFFFFFFull : mask;
+  if (threshold) krem = 0xFFFFFFFFFFFFFFFFull;
+  // 2. Compaction in index order within the slice (local index i = global
+  // index - lo), warp w over the block [g0, g1) as in select_mid.
+  const uint32_t span = (m + kMidThreads - 1) / kMidThreads * 32u;  // a multiple of 32
+  const uint32_t g0 = min(m, warp * span), g1 = min(m, g0 + span);  // warp-uniform
+  const bool rank_eq = !threshold && krem < bin_count;               // cluster-uniform
+  unsigned long long eq_rank = 0ull;  // equal keys before this warp's block, over the cluster
+  if (rank_eq) {
+    unsigned int weq = 0;
+    for (uint32_t g = g0; g < g1; g += 32u) {
+      const uint32_t i = g + lane;
+      weq += __popc(__ballot_sync(0xFFFFFFFFu, i < m && (key_of_bits(s_raw[i]) & cmask) == cut));
+    }
+    if (lane == 0) s_weq[warp] = weq;
+    __syncthreads();
+    unsigned int tot_eq;
+    eq_rank = warp_base_of(s_weq, warp, &tot_eq);
+    if (threadIdx.x == 0) eq0[rank] = tot_eq;
+    cluster.sync();  // equal-key counts posted
+    if (threadIdx.x < kClusterCtas) s_cnt[threadIdx.x] = eq0[threadIdx.x];
+    __syncthreads();
+    for (unsigned int r = 0; r < rank; ++r) eq_rank += s_cnt[r];
+  }
+  unsigned long long* const cut0 = cluster.map_shared_rank(&s_cut, 0);
+  unsigned int wacc = 0;
+  for (uint32_t g = g0; g < g1; g += 32u) {
+    const uint32_t i = g + lane;
+    const unsigned long long full = i < m ? key_of_bits(s_raw[i]) : 0ull;
+    const unsigned long long key = full & cmask;
+    const bool less = i < m && key < cut;
+    const bool eq = i < m && key == cut;
+    if (eq) *cut0 = full;  // every such key has the same full value
+    const unsigned int eqb = __ballot_sync(0xFFFFFFFFu, eq);
+    const bool take_eq = eq && (!rank_eq || eq_rank + __popc(eqb & lane_lt) < krem);
+    const unsigned int accb = __ballot_sync(0xFFFFFFFFu, less || take_eq);
+    if (lane == 0) acc_bits[g >> 5] = accb;
+    eq_rank += __popc(eqb);
+    wacc += __popc(accb);
+  }
+  if (lane == 0) s_wacc[warp] = wacc;
+  __syncthreads();
+  unsigned int n_cta;  // accepted in this slice
+  const unsigned long long pos_local = warp_base_of(s_wacc, warp, &n_cta);
+  if (threadIdx.x == 0) acc0[rank] = n_cta;
+  cluster.sync();  // accepted counts (and the cut's key) posted
+  if (threadIdx.x < kClusterCtas) s_cnt[threadIdx.x] = acc0[threadIdx.x];
+  __syncthreads();
+  unsigned long long cta_before = 0ull, n_acc = 0ull;
+#pragma unroll 1
+  for (int r = 0; r < kClusterCtas; ++r) {
+    if (r < static_cast<int>(rank)) cta_before += s_cnt[r];
+    n_acc += s_cnt[r];
+  }
+  // 3. Output in index order and this CTA's moment sums, as in select_mid
+  // (output positions offset by the accepted samples of the lower slices).
+  float cw[3] = {0.0f, 0.0f, 0.0f};
+  bool have_cw = false;  // warp-uniform
+  DF S1[3] = {DF{0.0f, 0.0f}, DF{0.0f, 0.0f}, DF{0.0f, 0.0f}};
+  DF S2[3] = {DF{0.0f, 0.0f}, DF{0.0f, 0.0f}, DF{0.0f, 0.0f}};
+  auto emit = [&](uint32_t il, unsigned long long p, float (&th)[3]) {
+    const uint32_t i = lo + il;
+    if (kTheta) {
+      th[0] = theta[i];
+      th[1] = theta[static_cast<size_t>(n) + i];
+      th[2] = theta[2 * static_cast<size_t>(n) + i];
+    } else {
+      ou_prior(prm, base + i, th[0], th[1], th[2]);
+    }
+    if (p == 0) {  // the moments' common shift, into every CTA
+#pragma unroll 1
+      for (int r = 0; r < kClusterCtas; ++r) {
+        float* const sh = cluster.map_shared_rank(s_shift, r);
+        sh[0] = th[0];
+        sh[1] = th[1];
+        sh[2] = th[2];
+      }
+    }
+    if (p < cap) {
+      idx_out[p] = i;
+      rec_out[p] = make_float4(th[0], th[1], th[2], static_cast<float>(__longlong_as_double(s_raw[il])));
+    }
+  };
+  const uint32_t n_groups = (g1 - g0 + 31u) / 32u;
+  const unsigned int word = static_cast<uint32_t>(lane) < n_groups ? acc_bits[(g0 >> 5) + lane] : 0u;
+  unsigned int before_g = __popc(word);
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, before_g, o);
+    if (lane >= o) before_g += y;
+  }
+  before_g -= __popc(word);
+  unsigned int busy = __ballot_sync(0xFFFFFFFFu, word != 0u);
+  unsigned int nw;  // accepted samples this warp sums
+  if (n_cta <= kMidList) {  // CTA-uniform: the list in the histogram's place
+    unsigned int* list = h;
+#pragma unroll 1
+    while (busy != 0u) {  // warp-uniform
+      const int q = __ffs(busy) - 1;
+      busy &= busy - 1u;
+      const unsigned int accb = __shfl_sync(0xFFFFFFFFu, word, q);
+      const unsigned int bq = __shfl_sync(0xFFFFFFFFu, before_g, q);
+      if ((accb >> lane) & 1u) list[pos_local + bq + __popc(accb & lane_lt)] = g0 + 32u * q + lane;
+    }
+    __syncthreads();
+    unsigned int mine_count = 0;
+#pragma unroll 1
+    for (uint32_t p0 = warp * 32u; p0 < n_cta; p0 += kMidThreads) {  // warp-uniform
+      const uint32_t p = p0 + lane;
+      const bool mine = p < n_cta;
+      float th[3] = {0.0f, 0.0f, 0.0f};
+      if (mine) emit(list[p], cta_before + p, th);
+      if (!have_cw) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) cw[d] = __shfl_sync(0xFFFFFFFFu, th[d], 0);
+        have_cw = true;
+      }
+      if (mine) {
+        add_moment(S1, S2, th, cw);
+        ++mine_count;
+      }
+    }
+    nw = __reduce_add_sync(0xFFFFFFFFu, mine_count);
+    if (lane == 0) s_wacc[warp] = nw;
+  } else {
+#pragma unroll 1
+    while (busy != 0u) {  // warp-uniform
+      const int q = __ffs(busy) - 1;
+      busy &= busy - 1u;
+      const unsigned int accb = __shfl_sync(0xFFFFFFFFu, word, q);
+      const unsigned long long pq = cta_before + pos_local + __shfl_sync(0xFFFFFFFFu, before_g, q);
+      const bool mine = (accb >> lane) & 1u;
+      float th[3] = {0.0f, 0.0f, 0.0f};
+      if (mine) emit(g0 + 32u * q + lane, pq + __popc(accb & lane_lt), th);
+      if (!have_cw) {
+        const int src = __ffs(accb) - 1;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) cw[d] = __shfl_sync(0xFFFFFFFFu, th[d], src);
+        have_cw = true;
+      }
+      if (mine) add_moment(S1, S2, th, cw);
+    }
+    nw = wacc;
+  }
+  cluster.sync();  // the common shift written into every CTA
+  if (cta_moment_sums<kMidWarps>(S1, S2, cw, nw, s_S1, s_S2, s_cw, s_wacc, s_shift) && lane == 0) {
+    DF* const S1_0 = cluster.map_shared_rank(c_S1, 0);
+    DF* const S2_0 = cluster.map_shared_rank(c_S2, 0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      S1_0[d * kClusterCtas + rank] = S1[d];
+      S2_0[d * kClusterCtas + rank] = S2[d];
+    }
+  }
+  cluster.sync();  // the CTAs' sums posted; the last barrier
+  if (rank == 0 && warp == 0) {
+    // the CTAs' sums (all about the common shift) added with a fixed tree
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      S1[d] = lane < kClusterCtas ? c_S1[d * kClusterCtas + lane] : DF{0.0f, 0.0f};
+      S2[d] = lane < kClusterCtas ? c_S2[d * kClusterCtas + lane] : DF{0.0f, 0.0f};
+    }
+#pragma unroll 1
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        S1[d] = df_add(S1[d], DF{__shfl_xor_sync(0xFFFFFFFFu, S1[d].hi, o), __shfl_xor_sync(0xFFFFFFFFu, S1[d].lo, o)});
+        S2[d] = df_add(S2[d], DF{__shfl_xor_sync(0xFFFFFFFFu, S2[d].hi, o), __shfl_xor_sync(0xFFFFFFFFu, S2[d].lo, o)});
+      }
+    }
+    store_moments(S1, S2, n_acc, s_shift, post_out);
+    if (lane == 0) {
+      *n_acc_out = n_acc;
+      if (eps_out) *eps_out = threshold ? eps_thr : key_to_double(s_cut);
+    }
+  }
+}
+
 unsigned long long host_dist_key(double d) {
   if (d != d) return 0xFFFFFFFFFFFFFFFFull;
   unsigned long long b;
@@ -871,9 +1192,14 @@ unsigned long long host_dist_key(double d) {
 
 size_t select_workspace_bytes(uint64_t n) { return WsLayout(n).total; }
 
-// The one-CTA selection keeps up to kMidMax distances in shared memory, above the
-// default 48 KB: the limit is raised once per device (a host call, made
-// before any stream capture that launches the selection).
+// The one-CTA and cluster selections keep up to kMidMax distances per CTA in
+// shared memory, above the default 48 KB: the limit is raised once per
+// device (a host call, made before any stream capture that launches the
+// selection), and the device is asked once whether a cluster of
+// kClusterCtas such CTAs fits at all (if not, those sizes take the
+// multi-launch path).
+std::atomic<unsigned long long> g_cluster_ok{0ull};
+
 cudaError_t select_prepare() {
   static std::atomic<unsigned long long> ready{0ull};
   int dev = 0;
@@ -881,13 +1207,40 @@ cudaError_t select_prepare() {
   if (e != cudaSuccess) return e;
   const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
   if (bit && (ready.load(std::memory_order_acquire) & bit)) return cudaSuccess;
-  e = cudaFuncSetAttribute(select_mid<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(kMidKeyBytes));
+  const int smem = static_cast<int>(kMidKeyBytes);
+  e = cudaFuncSetAttribute(select_mid<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(select_mid<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(select_mid<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kMidKeyBytes));
+    e = cudaFuncSetAttribute(select_cluster<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(select_cluster<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kClusterCtas);
+    cfg.blockDim = dim3(kMidThreads);
+    cfg.dynamicSmemBytes = kMidKeyBytes;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = kClusterCtas;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    const cudaError_t q = cudaOccupancyMaxActiveClusters(&clusters, select_cluster<false>, &cfg);
+    if (q == cudaSuccess && clusters > 0 && bit)
+      g_cluster_ok.fetch_or(bit, std::memory_order_acq_rel);
+    else if (q != cudaSuccess)
+      (void)cudaGetLastError();  // not sticky: the multi-launch path serves these sizes
+  }
   if (e == cudaSuccess && bit) ready.fetch_or(bit, std::memory_order_acq_rel);
   return e;
+}
+
+bool cluster_select_ok() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return false;
+  return (g_cluster_ok.load(std::memory_order_acquire) >> dev) & 1ull;
 }
 
 cudaError_t launch_select(const double* dist, uint32_t n, uint64_t k, double eps,
@@ -895,9 +1248,13 @@ cudaError_t launch_select(const double* dist, uint32_t n, uint64_t k, double eps
                           float* rec_out, uint64_t cap, uint64_t* n_acc_out, double* eps_out,
                           double* post_out, void* ws, cudaStream_t s) {
   const bool threshold = (k == 0);
-  if (n > 0 && n <= kMidMax) {
+  bool cluster_ok = false;
+  if (n > 0 && n <= kClusterMax) {
     cudaError_t e = select_prepare();
     if (e != cudaSuccess) return e;
+    cluster_ok = cluster_select_ok();
+  }
+  if (n > 0 && n <= kMidMax && (n <= kOneCtaMax || !cluster_ok)) {
     const unsigned long long cut = threshold ? host_dist_key(eps) : 0ull;
     const size_t smem = static_cast<size_t>(n) * sizeof(unsigned long long);
     if (theta)
@@ -910,6 +1267,22 @@ cudaError_t launch_select(const double* dist, uint32_t n, uint64_t k, double eps
                                                      theta, idx_out, reinterpret_cast<float4*>(rec_out), cap,
                                                      reinterpret_cast<unsigned long long*>(n_acc_out), eps_out,
                                                      post_out);
+    return cudaGetLastError();
+  }
+  if (n > 0 && n <= kClusterMax && cluster_ok) {
+    const unsigned long long cut = threshold ? host_dist_key(eps) : 0ull;
+    const uint32_t slice = ((n + kClusterCtas - 1) / kClusterCtas + 31u) & ~31u;
+    const size_t smem = static_cast<size_t>(slice) * sizeof(unsigned long long);
+    if (theta)
+      select_cluster<true><<<kClusterCtas, kMidThreads, smem, s>>>(
+          dist, n, k, threshold, cut, eps, P_, static_cast<uint32_t>(base), theta, idx_out,
+          reinterpret_cast<float4*>(rec_out), cap, reinterpret_cast<unsigned long long*>(n_acc_out), eps_out,
+          post_out);
+    else
+      select_cluster<false><<<kClusterCtas, kMidThreads, smem, s>>>(
+          dist, n, k, threshold, cut, eps, P_, static_cast<uint32_t>(base), theta, idx_out,
+          reinterpret_cast<float4*>(rec_out), cap, reinterpret_cast<unsigned long long*>(n_acc_out), eps_out,
+          post_out);
     return cudaGetLastError();
   }
   const WsLayout L(n);

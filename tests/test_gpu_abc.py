@@ -182,9 +182,17 @@ def _select_cases():
     # small sizes with ties (one CTA)
     for n in (4095, 4096, 4097, 2049):
         yield f"edge{n}", np.round(rng.exponential(size=n), 2)
-    # around the one-CTA selection's limit (24576 distances), heavy ties
-    for n in (24575, 24576, 24577, 30001):
+    # around the one-CTA selection's limit (12288 distances; 24576 where no
+    # cluster fits) and the one-CTA slices of the cluster, heavy ties
+    for n in (12288, 12289, 24575, 24576, 24577, 30001):
         yield f"mid{n}", np.round(rng.exponential(size=n), 1)
+    # the cluster selection (24577 .. 196608 distances over eight CTAs): ties
+    # spread over every slice, all keys equal, its largest size, and one more
+    # (the multi-launch path)
+    yield "cluster_ties150001", np.round(rng.exponential(size=150_001), 1)
+    yield "cluster_equal50000", np.full(50_000, 0.25)
+    yield "cluster_max196608", np.round(rng.exponential(size=196_608), 2)
+    yield "over_cluster196609", rng.uniform(0, 1, size=196_609)
     # distinct values: the radix passes stop once one key is left under the
     # prefix (after two or three passes here) ...
     for n in (1000, 24576, 30001):
@@ -236,6 +244,30 @@ def test_select_exact_on_given_distances(case):
         assert to_np(sel["eps"])[0] == eps or (math.isinf(eps) and math.isinf(to_np(sel["eps"])[0]))
 
 
+@pytest.mark.parametrize("n,k", [(65_536, 655), (150_001, 40_000)])
+def test_cluster_selection_redraws_theta_bit_identically(n, k):
+    """The cluster selection (24577 .. 196608 distances) with theta given and
+    with theta redrawn from the prior counter: the same records and moments
+    bit for bit, k accepted in index order, and the records' theta that of
+    the accepted samples."""
+    binding = require_gpu()
+    w = workloads.abc_small()
+    out = binding.abc_prior_predictive(w.model, w.y_obs, n, w.seed)
+    sel = binding.abc_select(out["dist"], k=k, model=w.model, seed=w.seed, theta=out["theta"])
+    sel_regen = binding.abc_select(out["dist"], k=k, model=w.model, seed=w.seed)
+    torch.cuda.synchronize()
+    d_g = to_np(out["dist"])
+    idx_g = to_np(sel["idx"]).astype(np.int64)
+    np.testing.assert_array_equal(idx_g, oracle.select_topk(d_g, k).astype(np.int64))
+    np.testing.assert_array_equal(to_np(sel_regen["rec"]), to_np(sel["rec"]))
+    np.testing.assert_array_equal(to_np(sel_regen["post"]), to_np(sel["post"]))
+    th_g = to_np(out["theta"]).T
+    np.testing.assert_array_equal(to_np(sel["rec"])[:, :3], th_g[idx_g])
+    mean_o, var_o = oracle.moments(th_g.astype(np.float64), idx_g.astype(np.uint64))
+    np.testing.assert_allclose(to_np(sel["post"])[:3], mean_o, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(to_np(sel["post"])[3:], var_o, rtol=1e-10)
+
+
 def test_eps_infinity_accepts_every_sample():
     binding = require_gpu()
     w = workloads.abc_small()
@@ -250,10 +282,11 @@ def test_eps_infinity_accepts_every_sample():
     np.testing.assert_allclose(post[3:], th.var(axis=1, ddof=1), rtol=1e-10)
 
 
-def test_cap_smaller_than_accepted_count():
+@pytest.mark.parametrize("n", [10_000, 60_000])
+def test_cap_smaller_than_accepted_count(n):
     binding = require_gpu()
-    d = torch.linspace(0, 1, 10_000, dtype=torch.float64, device="cuda")
-    th = torch.zeros((3, 10_000), dtype=torch.float32, device="cuda")
+    d = torch.linspace(0, 1, n, dtype=torch.float64, device="cuda")
+    th = torch.zeros((3, n), dtype=torch.float32, device="cuda")
     sel = binding.abc_select(d, k=0, eps=0.5, theta=th, cap=100)
     torch.cuda.synchronize()
     assert int(to_np(sel["n_acc"])[0]) == int((to_np(d) <= 0.5).sum())
