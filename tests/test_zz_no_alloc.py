@@ -71,6 +71,15 @@ def test_static_scratch_matches_workspace_version_on_two_calls():
     _same(s2, r2)
     assert int(s2["n_acc"].cpu()[0]) == int((d <= eps).sum())
 
+    # a size the cluster selection serves (no scratch at all), theta given
+    d4 = torch.from_numpy(d[:60_000].copy()).cuda()
+    th4 = th[:, :60_000].contiguous()
+    s4 = binding.abc_select_static(d4, k=600, theta=th4)
+    r4 = binding.abc_select(d4, k=600, theta=th4)
+    torch.cuda.synchronize()
+    _same(s4, r4)
+    assert int(s4["n_acc"].cpu()[0]) == 600
+
     # and once more in top-k mode on the second array (the scratch keeps state between calls)
     s3 = binding.abc_select_static(dt, k=777, theta=th)
     r3 = binding.abc_select(dt, k=777, theta=th)
