@@ -193,6 +193,8 @@ def _select_cases():
     yield "cluster_equal50000", np.full(50_000, 0.25)
     yield "cluster_max196608", np.round(rng.exponential(size=196_608), 2)
     yield "over_cluster196609", rng.uniform(0, 1, size=196_609)
+    # the multi-launch path with heavy ties across its 4096-distance tiles
+    yield "tiles_ties300001", np.round(rng.exponential(size=300_001), 1)
     # distinct values: the radix passes stop once one key is left under the
     # prefix (after two or three passes here) ...
     for n in (1000, 24576, 30001):
