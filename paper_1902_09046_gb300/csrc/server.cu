@@ -14,6 +14,7 @@
 //
 // Nothing on the GPU waits for the host: completion is observed by polling
 // CUDA events, and host waits have timeouts.
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -116,6 +117,10 @@ struct SlotHost {
   double p;
   double lambda;
 };
+// launch_job copies (n_acc, eps, post) and (count, p) back in one piece each
+static_assert(offsetof(SlotHost, eps) == 8 && offsetof(SlotHost, post) == 16 &&
+                  offsetof(SlotHost, p) == offsetof(SlotHost, count) + 8,
+              "the result fields are contiguous");
 
 struct Slot {
   cudaStream_t stream = nullptr;     // lowest priority: large jobs
@@ -220,29 +225,28 @@ int launch_job(ppabc_server* S, uint64_t id, int si) {
     uint32_t* idx = reinterpret_cast<uint32_t*>(k);
     float* rec = reinterpret_cast<float*>(k + align256(sizeof(uint32_t) * r.k));
     char* tail = k + align256(sizeof(uint32_t) * r.k) + align256(16 * r.k);
+    // the count, epsilon and moments side by side, as in SlotHost, so one
+    // copy brings them back
     uint64_t* n_acc = reinterpret_cast<uint64_t*>(tail);
-    double* eps = reinterpret_cast<double*>(tail + 256);
-    double* post = reinterpret_cast<double*>(tail + 512);
+    double* eps = reinterpret_cast<double*>(tail + 8);
+    double* post = reinterpret_cast<double*>(tail + 16);
     e = launch_em_ou(P, 0, static_cast<uint32_t>(r.n_samples), nullptr, nullptr, dist, st);
     if (e == cudaSuccess)
       e = launch_select(dist, static_cast<uint32_t>(r.n_samples), r.k, 0.0, P, 0, nullptr, idx, rec, r.k,
                         n_acc, eps, post, sel_ws, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&sl.host->n_acc, n_acc, 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&sl.host->eps, eps, 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.host->post, post, 48, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&sl.host->n_acc, tail, 64, cudaMemcpyDeviceToHost, st);
     J.cap = r.k;
   } else {
     const ppabc_request& r = J.req;
     double* lam = reinterpret_cast<double*>(w);
     uint64_t* counts = reinterpret_cast<uint64_t*>(w + 256);
-    double* p = reinterpret_cast<double*>(w + 512);
+    double* p = reinterpret_cast<double*>(w + 264);  // next to the count, as in SlotHost
     sl.host->lambda = r.lambda;
     e = cudaMemcpyAsync(lam, &sl.host->lambda, 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
       e = launch_pvalue(lam, 1, r.n_obs, static_cast<uint32_t>(r.m_sets), 0, r.ybar_obs, r.seed, counts, p,
                         nullptr, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&sl.host->count, counts, 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&sl.host->p, p, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&sl.host->count, counts, 16, cudaMemcpyDeviceToHost, st);
   }
   if (e == cudaSuccess) e = cudaEventRecord(sl.done, st);
   if (e != cudaSuccess) {
